@@ -1,0 +1,576 @@
+/*
+ * FP64 CPU oracle for randomly pivoted Cholesky (Epperly, Tropp, Webber,
+ * "Embrace rejection: Kernel matrix approximation by accelerated randomly
+ * pivoted Cholesky", arXiv 2410.03969).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * restatement of the method that the CUDA path is checked against.  Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg load it.
+ * It shares no code, header, table or helper with the CUDA library.
+ *
+ * What is here, each written from the paper's text:
+ *   - orc_philox4x32_10 / orc_u53: the counter-based random source.  The
+ *     paper only says "Rand()" (Algorithm 1); the generator is Philox4x32-10
+ *     from Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+ *     1, 2, 3" (SC'11), written from that description.
+ *   - orc_kernel_entry: Gaussian (Eq. "gaussian", Sec. 1.2), Matern-5/2
+ *     (Sec. 3.2) and the l2-Laplace exp(-||x-y||/sigma), all through direct
+ *     differences sum_l (x_l - y_l)^2, as the paper's block experiments do
+ *     (App. A.1, last paragraph).
+ *   - orc_sample: one draw from the distribution w / sum(w) (Eq. 1.3 and
+ *     the proposal step of Algorithm 2).
+ *   - orc_reject_chol: RejectionSampleSubmatrix, Algorithm 1.
+ *   - orc_rpc_plain: simple RPCholesky, Algorithm 6 (appendix).
+ *   - orc_rpc_accel: accelerated RPCholesky, Algorithm 2, calling Algorithm 1.
+ *   - orc_fixed_pivot_factor: Cholesky with a given pivot order; it gives the
+ *     exact Nystrom approximation A(:,S) A(S,S)^+ A(S,:) of Sec. 2.1 so that
+ *     a pivot list produced elsewhere can be re-evaluated in FP64.
+ *
+ * Readings taken where the paper is silent (each also listed in the design
+ * notes of the repository):
+ *   - random stream: Philox key = (seed low word, seed high word); the block
+ *     for round r, proposal slot j, instance m uses counter (j, r, 0, m);
+ *     words (w0,w1) give the proposal uniform, (w2,w3) the acceptance
+ *     uniform.  Simple RPCholesky step i uses counter (0, i, 0, m), words
+ *     (w0,w1), the same uniform as accelerated round i slot 0.
+ *   - uniform from two words: ((w_a >> 5) * 2^26 + (w_b >> 6)) * 2^-53.
+ *   - proposal map: W = sum of weights in index order, C_j the inclusive
+ *     prefix sum in index order, pick min{ j : C_j > U*W }; if rounding
+ *     leaves none, the largest j with w_j > 0.  Zero weights never chosen.
+ *   - acceptance (Algorithm 1 test "u_i * Rand() < h_ii"): u_i is the weight
+ *     d[s'_i] that proposal i was drawn with (the rejection-sampling box of
+ *     Sec. 2.1 divides by the proposal weight); strict "<" in FP64.
+ *   - reaching exactly k: Algorithm 1 stops as soon as the total rank is k;
+ *     the remaining proposals of that round are ignored.
+ *   - the diagonal u is clamped at zero after every round / step
+ *     (Algorithm 2, last line), in both algorithms.
+ *   - simple RPCholesky: F(:,i) = g / sqrt(g_s) with g_s taken from the
+ *     freshly formed column (Algorithm 6).  If g_s <= 0 (only possible
+ *     through rounding) the step adds no column, sets d[s] = 0 and moves on.
+ *   - G = R L^{-*} (Algorithm 2, step 3) is solved row by row by forward
+ *     substitution with the lower-triangular L.
+ *
+ * Floating point: everything in IEEE double; compiled with
+ * -ffp-contract=off so that results do not depend on FMA contraction of the
+ * host compiler (x86-64 and aarch64 give the same bits).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+
+enum { ORC_GAUSSIAN = 0, ORC_LAPLACE_L2 = 1, ORC_MATERN52 = 2 };
+
+static int orc_threads = 1;
+
+int orc_set_threads(int n)
+{
+    orc_threads = n < 1 ? 1 : n;
+#ifdef _OPENMP
+    return orc_threads;
+#else
+    orc_threads = 1;
+    return 1;
+#endif
+}
+
+int orc_has_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11).  One round maps (c0,c1,c2,c3) with
+ * key (k0,k1) through two 32x32->64 multiplications:
+ *   (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2
+ *   c' = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0)
+ * and the key is bumped by the Weyl constants between rounds.            */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* A uniform double in [0, 1 - 2^-53] from 27 + 26 random bits. */
+double orc_u53(uint32_t a, uint32_t b)
+{
+    uint64_t hi = (uint64_t)(a >> 5);
+    uint64_t lo = (uint64_t)(b >> 6);
+    return (double)(hi * 67108864u + lo) * (1.0 / 9007199254740992.0);
+}
+
+/* The two uniforms of one Philox block: proposal (w0,w1), acceptance (w2,w3). */
+void orc_uniform_pair(uint64_t seed, uint32_t slot, uint32_t round, uint32_t inst,
+                      double* u_prop, double* u_acc)
+{
+    uint32_t ctr[4] = {slot, round, 0u, inst};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    if (u_prop) *u_prop = orc_u53(w[0], w[1]);
+    if (u_acc) *u_acc = orc_u53(w[2], w[3]);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Kernel functions phi(r) with kappa(x,x') = phi(||x - x'||).             */
+static double orc_phi_from_r2(int kind, double sigma, double r2)
+{
+    if (r2 < 0.0) r2 = 0.0;
+    switch (kind) {
+    case ORC_GAUSSIAN:
+        return exp(-r2 / (2.0 * sigma * sigma));
+    case ORC_LAPLACE_L2: {
+        double r = sqrt(r2);
+        return exp(-r / sigma);
+    }
+    case ORC_MATERN52: {
+        double r = sqrt(r2);
+        double t = sqrt(5.0) * r / sigma;
+        return (1.0 + t + 5.0 * r2 / (3.0 * sigma * sigma)) * exp(-t);
+    }
+    default:
+        return NAN;
+    }
+}
+
+double orc_phi(int kind, double sigma, double r2) { return orc_phi_from_r2(kind, sigma, r2); }
+
+/* kappa(x_i, x_j) by direct differences; the diagonal is phi(0) = 1 exactly. */
+static double orc_point_entry(int kind, double sigma, const float* X, int d, int64_t i, int64_t j)
+{
+    if (i == j) return 1.0;
+    const float* xi = X + i * (int64_t)d;
+    const float* xj = X + j * (int64_t)d;
+    double r2 = 0.0;
+    for (int l = 0; l < d; ++l) {
+        double t = (double)xi[l] - (double)xj[l];
+        r2 += t * t;
+    }
+    return orc_phi_from_r2(kind, sigma, r2);
+}
+
+/* A matrix seen through the submatrix access model: either kernel entries
+ * of points X (N x d, row-major, float) or an explicit dense psd matrix
+ * (N x N, row-major, double) used by the tests.                           */
+typedef struct {
+    const float* X;
+    int d;
+    int kind;
+    double sigma;
+    const double* A;
+    int64_t N;
+} orc_matrix;
+
+static double orc_entry(const orc_matrix* M, int64_t i, int64_t j)
+{
+    if (M->A) return M->A[i * M->N + j];
+    return orc_point_entry(M->kind, M->sigma, M->X, M->d, i, j);
+}
+
+double orc_kernel_entry(int kind, double sigma, const float* X, int d, int64_t i, int64_t j)
+{
+    return orc_point_entry(kind, sigma, X, d, i, j);
+}
+
+/* ---------------------------------------------------------------------- */
+/* One draw from w / sum(w):  j* = min{ j : C_j > U * W }.                  */
+int64_t orc_sample(const double* w, int64_t N, double W, double U)
+{
+    double target = U * W;
+    double c = 0.0;
+    for (int64_t j = 0; j < N; ++j) {
+        c += w[j];
+        if (w[j] > 0.0 && c > target) return j;
+    }
+    for (int64_t j = N - 1; j >= 0; --j)
+        if (w[j] > 0.0) return j;
+    return -1;
+}
+
+double orc_weight_total(const double* w, int64_t N)
+{
+    double W = 0.0;
+    for (int64_t j = 0; j < N; ++j) W += w[j];
+    return W;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 1 (RejectionSampleSubmatrix) on the b x b psd matrix H
+ * (row-major, overwritten).  u[i] is the proposal weight of proposal i,
+ * uacc[i] its acceptance uniform.  At most max_accept pivots are accepted.
+ * Outputs: acc[0..n) local indices of accepted proposals in order; Lc, an
+ * n x n lower-triangular matrix (row-major, leading dimension b) with
+ * H_in(acc,acc) = Lc Lc^*.                                                */
+int orc_reject_chol(double* H, int32_t b, const double* u, const double* uacc,
+                    int32_t max_accept, int32_t* acc, double* Lc, int32_t* n_out)
+{
+    if (b < 1 || !H || !u || !uacc || !acc || !Lc || !n_out) return ORC_EINVAL;
+    double* L = (double*)calloc((size_t)b * b, sizeof(double));
+    if (!L) return ORC_ENOMEM;
+    int32_t n = 0;
+    for (int32_t i = 0; i < b; ++i) {
+        if (n >= max_accept) break;
+        double hii = H[(int64_t)i * b + i];
+        if (u[i] * uacc[i] < hii) {
+            acc[n++] = i;
+            double piv = sqrt(hii);
+            for (int32_t j = i; j < b; ++j) L[(int64_t)j * b + i] = H[(int64_t)j * b + i] / piv;
+            for (int32_t j = i + 1; j < b; ++j)
+                for (int32_t l = i + 1; l <= j; ++l) {
+                    double upd = L[(int64_t)j * b + i] * L[(int64_t)l * b + i];
+                    H[(int64_t)j * b + l] -= upd;
+                    if (l != j) H[(int64_t)l * b + j] -= upd;
+                }
+        }
+    }
+    for (int32_t a = 0; a < n; ++a)
+        for (int32_t c = 0; c < b; ++c)
+            Lc[(int64_t)a * b + c] = (c < n) ? L[(int64_t)acc[a] * b + acc[c]] : 0.0;
+    *n_out = n;
+    free(L);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 6, simple RPCholesky.  F is N x k, row-major, ld = k, zeroed by
+ * the caller or here.  S receives the pivots.  d receives the final
+ * (clamped) residual diagonal.  Returns the rank reached in *rank.        */
+static int rpc_plain_impl(const orc_matrix* M, int64_t k, uint64_t seed, uint32_t inst,
+                          double* F, int64_t* S, double* d, int64_t* rank_out)
+{
+    const int64_t N = M->N;
+    if (k < 0 || k > N) return ORC_EINVAL;
+    memset(F, 0, sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
+    for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    double* g = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!g) return ORC_ENOMEM;
+    int64_t rank = 0;
+    for (int64_t step = 0; step < 4 * k + 64 && rank < k; ++step) {
+        double W = orc_weight_total(d, N);
+        if (!(W > 0.0)) break;
+        double U;
+        orc_uniform_pair(seed, 0u, (uint32_t)step, inst, &U, NULL);
+        int64_t s = orc_sample(d, N, W, U);
+        if (s < 0) break;
+        const int64_t i = rank;
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t r = 0; r < N; ++r) {
+            double acc = orc_entry(M, r, s);
+            for (int64_t m = 0; m < i; ++m) acc -= F[r * k + m] * F[s * k + m];
+            g[r] = acc;
+        }
+        double gs = g[s];
+        if (!(gs > 0.0)) {
+            d[s] = 0.0;
+            continue;
+        }
+        double piv = sqrt(gs);
+        S[i] = s;
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t r = 0; r < N; ++r) {
+            double f = g[r] / piv;
+            F[r * k + i] = f;
+            double v = d[r] - f * f;
+            d[r] = v > 0.0 ? v : 0.0;
+        }
+        rank = i + 1;
+    }
+    free(g);
+    *rank_out = rank;
+    return ORC_OK;
+}
+
+/* Algorithm 2, accelerated RPCholesky with Algorithm 1 inside.
+ * k: target rank (stop exactly there); T: block size b; max_rounds: stop
+ * after this many rounds (<= 0: no limit besides k).  F: N x k row-major,
+ * ld = k.  Per-round sizes are written to round_sizes (if not NULL, length
+ * >= number of rounds).  accept_rule 0: u_i = d[s'_i] (proposal weight);
+ * 1: u_i = h_ii at entry of Algorithm 1 (the literal line of Algorithm 1).
+ * dpre (if not NULL) receives the residual diagonal of the last round
+ * before clamping.                                                        */
+static int rpc_accel_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t max_rounds,
+                          uint64_t seed, uint32_t inst, int accept_rule, double* F, int64_t* S,
+                          double* d, double* dpre, int64_t* rank_out, int64_t* rounds_out,
+                          int32_t* round_sizes, int64_t round_sizes_cap)
+{
+    const int64_t N = M->N;
+    if (k < 0 || k > N || T < 1) return ORC_EINVAL;
+    memset(F, 0, sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
+    for (int64_t j = 0; j < N; ++j) {
+        d[j] = orc_entry(M, j, j);
+        if (dpre) dpre[j] = d[j];
+    }
+    int64_t* prop = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
+    double* u = (double*)malloc(sizeof(double) * (size_t)T);
+    double* ua = (double*)malloc(sizeof(double) * (size_t)T);
+    double* H = (double*)malloc(sizeof(double) * (size_t)T * T);
+    double* L = (double*)malloc(sizeof(double) * (size_t)T * T);
+    int32_t* acc = (int32_t*)malloc(sizeof(int32_t) * (size_t)T);
+    int64_t* Si = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
+    if (!prop || !u || !ua || !H || !L || !acc || !Si) {
+        free(prop); free(u); free(ua); free(H); free(L); free(acc); free(Si);
+        return ORC_ENOMEM;
+    }
+    int64_t rank = 0, round = 0;
+    while (rank < k && (max_rounds <= 0 || round < max_rounds)) {
+        /* Step 1: propose T iid pivots from u = d. */
+        double W = orc_weight_total(d, N);
+        if (!(W > 0.0)) break;
+        for (int32_t j = 0; j < T; ++j) {
+            double Up, Ua;
+            orc_uniform_pair(seed, (uint32_t)j, (uint32_t)round, inst, &Up, &Ua);
+            prop[j] = orc_sample(d, N, W, Up);
+            u[j] = d[prop[j]];
+            ua[j] = Ua;
+        }
+        /* Step 2: H = A(S',S') - F(S',:) F(S',:)^*, then Algorithm 1. */
+        for (int32_t a = 0; a < T; ++a)
+            for (int32_t b = 0; b < T; ++b) {
+                double h = orc_entry(M, prop[a], prop[b]);
+                for (int64_t m = 0; m < rank; ++m) h -= F[prop[a] * k + m] * F[prop[b] * k + m];
+                H[(int64_t)a * T + b] = h;
+            }
+        if (accept_rule == 1)
+            for (int32_t a = 0; a < T; ++a) u[a] = H[(int64_t)a * T + a];
+        int32_t n = 0;
+        int rc = orc_reject_chol(H, T, u, ua, (int32_t)(k - rank), acc, L, &n);
+        if (rc != ORC_OK) {
+            free(prop); free(u); free(ua); free(H); free(L); free(acc); free(Si);
+            return rc;
+        }
+        if (round_sizes && round < round_sizes_cap) round_sizes[round] = n;
+        for (int32_t a = 0; a < n; ++a) {
+            Si[a] = prop[acc[a]];
+            S[rank + a] = Si[a];
+        }
+        /* Step 3: G = (A(:,S_i) - F F(S_i,:)^*) L^{-*}; F <- [F G];
+         *         u <- max(u - rowsumsq(G), 0).                           */
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t r = 0; r < N; ++r) {
+            double Grow[1024];
+            double* G = Grow;
+            double* Gheap = NULL;
+            if (n > 1024) {
+                Gheap = (double*)malloc(sizeof(double) * (size_t)n);
+                G = Gheap;
+            }
+            for (int32_t j = 0; j < n; ++j) {
+                double rr = orc_entry(M, r, Si[j]);
+                for (int64_t m = 0; m < rank; ++m) rr -= F[r * k + m] * F[Si[j] * k + m];
+                G[j] = rr;
+            }
+            for (int32_t j = 0; j < n; ++j) {
+                double v = G[j];
+                for (int32_t l = 0; l < j; ++l) v -= G[l] * L[(int64_t)j * T + l];
+                G[j] = v / L[(int64_t)j * T + j];
+            }
+            double rsq = 0.0;
+            for (int32_t j = 0; j < n; ++j) {
+                F[r * k + rank + j] = G[j];
+                rsq += G[j] * G[j];
+            }
+            double v = d[r] - rsq;
+            if (dpre) dpre[r] = v;
+            d[r] = v > 0.0 ? v : 0.0;
+            free(Gheap);
+        }
+        rank += n;
+        round += 1;
+    }
+    free(prop); free(u); free(ua); free(H); free(L); free(acc); free(Si);
+    *rank_out = rank;
+    if (rounds_out) *rounds_out = round;
+    return ORC_OK;
+}
+
+/* Cholesky with the given pivot order (the deterministic recursion of
+ * Algorithm 6 with s_i fixed): F is N x k row-major (ld = k); d receives
+ * diag(A - F F^*).  A pivot whose residual is <= 0 adds a zero column.
+ * Returns tr(A - F F^*) in *trace_err.                                    */
+static int fixed_pivot_impl(const orc_matrix* M, const int64_t* S, int64_t k, double* F,
+                            double* d, double* trace_err)
+{
+    const int64_t N = M->N;
+    memset(F, 0, sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
+    for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    double* g = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!g) return ORC_ENOMEM;
+    for (int64_t i = 0; i < k; ++i) {
+        int64_t s = S[i];
+        if (s < 0 || s >= N) {
+            free(g);
+            return ORC_EINVAL;
+        }
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t r = 0; r < N; ++r) {
+            double acc = orc_entry(M, r, s);
+            for (int64_t m = 0; m < i; ++m) acc -= F[r * k + m] * F[s * k + m];
+            g[r] = acc;
+        }
+        double gs = g[s];
+        if (!(gs > 0.0)) continue;
+        double piv = sqrt(gs);
+        for (int64_t r = 0; r < N; ++r) {
+            double f = g[r] / piv;
+            F[r * k + i] = f;
+            d[r] -= f * f;
+        }
+    }
+    double t = 0.0;
+    for (int64_t j = 0; j < N; ++j) t += d[j];
+    *trace_err = t;
+    free(g);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Exported entry points.  X: N x d float row-major (points) or NULL;
+ * A: N x N double row-major (explicit psd matrix) or NULL; exactly one of
+ * the two is given.                                                       */
+static int make_matrix(orc_matrix* M, const float* X, int d, int kind, double sigma,
+                       const double* A, int64_t N)
+{
+    if (N < 1) return ORC_EINVAL;
+    if ((X == NULL) == (A == NULL)) return ORC_EINVAL;
+    if (X && (d < 1 || !(sigma > 0.0) || kind < 0 || kind > 2)) return ORC_EINVAL;
+    M->X = X;
+    M->d = d;
+    M->kind = kind;
+    M->sigma = sigma;
+    M->A = A;
+    M->N = N;
+    return ORC_OK;
+}
+
+int orc_rpc_plain(const float* X, int d, int kind, double sigma, const double* A, int64_t N,
+                  int64_t k, uint64_t seed, uint32_t inst, double* F, int64_t* S, double* dres,
+                  int64_t* rank)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, X, d, kind, sigma, A, N);
+    if (rc) return rc;
+    return rpc_plain_impl(&M, k, seed, inst, F, S, dres, rank);
+}
+
+int orc_rpc_accel(const float* X, int d, int kind, double sigma, const double* A, int64_t N,
+                  int64_t k, int32_t T, int64_t max_rounds, uint64_t seed, uint32_t inst,
+                  int accept_rule, double* F, int64_t* S, double* dres, double* dpre,
+                  int64_t* rank, int64_t* rounds, int32_t* round_sizes, int64_t round_sizes_cap)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, X, d, kind, sigma, A, N);
+    if (rc) return rc;
+    return rpc_accel_impl(&M, k, T, max_rounds, seed, inst, accept_rule, F, S, dres, dpre, rank,
+                          rounds, round_sizes, round_sizes_cap);
+}
+
+int orc_fixed_pivot_factor(const float* X, int d, int kind, double sigma, const double* A,
+                           int64_t N, const int64_t* S, int64_t k, double* F, double* dres,
+                           double* trace_err)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, X, d, kind, sigma, A, N);
+    if (rc) return rc;
+    return fixed_pivot_impl(&M, S, k, F, dres, trace_err);
+}
+
+/* Many independent runs on one matrix (instances inst0 .. inst0+n-1), for
+ * the distribution tests; only the first k pivots of each are kept.
+ * algo 0: simple RPCholesky; algo 1: accelerated with block T.            */
+int orc_pivots_many(const float* X, int d, int kind, double sigma, const double* A, int64_t N,
+                    int algo, int64_t k, int32_t T, uint64_t seed, uint32_t inst0, int64_t n,
+                    int64_t* S_out, int64_t* rank_out)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, X, d, kind, sigma, A, N);
+    if (rc) return rc;
+    double* F = (double*)malloc(sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
+    double* dd = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!F || !dd) {
+        free(F);
+        free(dd);
+        return ORC_ENOMEM;
+    }
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t rank = 0;
+        uint32_t inst = inst0 + (uint32_t)t;
+        if (algo == 0)
+            rc = rpc_plain_impl(&M, k, seed, inst, F, S_out + t * k, dd, &rank);
+        else
+            rc = rpc_accel_impl(&M, k, T, 0, seed, inst, 0, F, S_out + t * k, dd, NULL, &rank,
+                                NULL, NULL, 0);
+        if (rc) break;
+        rank_out[t] = rank;
+    }
+    free(F);
+    free(dd);
+    return rc;
+}
+
+/* Residual trace after t rounds of accelerated RPCholesky for many runs
+ * (Lemma "central error bound" check).                                    */
+int orc_accel_trace_many(const double* A, int64_t N, int32_t T, int64_t rounds, uint64_t seed,
+                         uint32_t inst0, int64_t n, double* trace_out)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, NULL, 0, 0, 1.0, A, N);
+    if (rc) return rc;
+    double* F = (double*)malloc(sizeof(double) * (size_t)N * (size_t)N);
+    double* dd = (double*)malloc(sizeof(double) * (size_t)N);
+    int64_t* S = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    if (!F || !dd || !S) {
+        free(F); free(dd); free(S);
+        return ORC_ENOMEM;
+    }
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t rank = 0, nr = 0;
+        rc = rpc_accel_impl(&M, N, T, rounds, seed, inst0 + (uint32_t)t, 0, F, S, dd, NULL, &rank,
+                            &nr, NULL, 0);
+        if (rc) break;
+        /* exact residual trace from the factor: tr(A) - ||F||_F^2 */
+        double tr = 0.0;
+        for (int64_t j = 0; j < N; ++j) {
+            double v = A[j * N + j];
+            for (int64_t m = 0; m < rank; ++m) v -= F[j * N + m] * F[j * N + m];
+            tr += v;
+        }
+        trace_out[t] = tr;
+    }
+    free(F); free(dd); free(S);
+    return rc;
+}
