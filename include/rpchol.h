@@ -1,0 +1,187 @@
+/*
+ * rpchol.h -- C ABI of the GB300 (sm_103a) implementation of accelerated
+ * randomly pivoted Cholesky (Epperly, Tropp, Webber, arXiv 2410.03969).
+ *
+ * The library turns a kernel matrix A = K(X, X) that is never formed into a
+ * rank-k factor F with A ~= F F^*, by the block rounds of Algorithm 2
+ * ("Accelerated RPCholesky: standard implementation", Sec. 2.3):
+ *   (a) propose T pivots iid from the residual diagonal d (Algorithm 2,
+ *       step 1; Eq. 1.3),
+ *   (b) form H = A(S',S') - F(S',:) F(S',:)^* and thin the proposals with
+ *       RejectionSampleSubmatrix (Algorithm 1, Sec. 2.2),
+ *   (c) G = (A(:,S) - F F(S,:)^*) L^{-*}, F <- [F G] (Algorithm 2, step 3),
+ *   (d) d <- max(d - rowsumsq(G), 0) (Algorithm 2, last two lines).
+ * Simple RPCholesky (Algorithm 6, appendix) is provided as the GPU baseline.
+ * Every step runs in the library's own CUDA kernels; there is no CPU path.
+ *
+ * Conventions shared by every entry point:
+ *   - Status codes only; nothing throws or aborts across this boundary.
+ *     rpchol_last_error() returns a thread-local description of the last
+ *     failure on the calling thread.
+ *   - Device memory is owned by the library (allocated at create, released
+ *     at destroy) through the allocator given in rpchol_opts, or
+ *     cudaMallocAsync/cudaFreeAsync on the context's stream when none is
+ *     given.
+ *   - Every call that launches work is asynchronous on the context's
+ *     stream, unless stated otherwise.  A context must not be used from two
+ *     threads at once.
+ *   - Points X are row-major N x d (the paper's d x N column matrix
+ *     X = [x_1 ... x_N] of App. A.1, stored point by point).
+ *   - The factor F is row-major N x ldF (ldF >= k_max, a multiple of 32);
+ *     column j holds the j-th accepted pivot's column; columns >= rank are
+ *     unspecified.  Pivots are 0-based row indices (int64).
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed low 32 bits, seed high 32 bits); round r, proposal slot j of
+ *     instance m uses counter (j, r, 0, m); words (w0,w1) give the proposal
+ *     uniform, (w2,w3) the acceptance uniform, each as
+ *     ((w_a >> 5) 2^26 + (w_b >> 6)) 2^-53.  Simple RPCholesky step i uses
+ *     counter (0, i, 0, m), words (w0,w1).
+ */
+#ifndef RPCHOL_H
+#define RPCHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RPCHOL_OK = 0,
+    RPCHOL_EINVAL = 1,     /* invalid argument; nothing was launched */
+    RPCHOL_ENOMEM = 2,     /* device or host allocation failed */
+    RPCHOL_ECUDA = 3,      /* a CUDA runtime call failed; see rpchol_last_error */
+    RPCHOL_ETIMEOUT = 4,   /* round limit reached or a bounded device wait expired */
+    RPCHOL_EBUSY = 5,      /* resource in use (server slots, budget) */
+    RPCHOL_ECANCELLED = 6, /* job cancelled before it ran */
+    RPCHOL_ENUMERIC = 7    /* non-finite value or non-positive pivot met on the device */
+} rpchol_status;
+
+/* kappa(x, y) = phi(||x - y||_2), phi(0) = 1 so diag A = 1.
+ *   GAUSSIAN    exp(-r^2 / (2 sigma^2))                     (Sec. 1.2)
+ *   LAPLACE_L2  exp(-r / sigma)
+ *   MATERN52    (1 + sqrt5 r/sigma + 5 r^2/(3 sigma^2)) exp(-sqrt5 r/sigma)
+ *                                                           (Sec. 3.2)     */
+typedef enum { RPCHOL_GAUSSIAN = 0, RPCHOL_LAPLACE_L2 = 1, RPCHOL_MATERN52 = 2 } rpchol_kernel_kind;
+
+/* FP64: every step in IEEE double (parity mode).
+ * MIXED: F stored in FP32; the kernel-column and Schur contractions run in
+ * single-precision arithmetic with FP32 accumulation (compensated split
+ * products on the tensor-core path); the T x T rejection-sampling Cholesky,
+ * L^{-1} and the residual-diagonal accumulation stay in FP64.             */
+typedef enum { RPCHOL_FP64 = 0, RPCHOL_MIXED = 1 } rpchol_precision;
+
+typedef enum { RPCHOL_DT_F32 = 0, RPCHOL_DT_F64 = 1 } rpchol_dtype;
+
+typedef void* (*rpchol_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*rpchol_free_fn)(void* ptr, void* stream, void* user);
+
+typedef struct {
+    int32_t precision;       /* rpchol_precision */
+    int32_t use_graph;       /* 1: round loop as a CUDA graph with a device-side
+                                while-condition (default); 0: host loop */
+    uint32_t instance;       /* Philox counter word 3 (independent streams) */
+    int32_t profile;         /* 1: host-driven loop with CUDA events around every
+                                kernel phase on the context's stream; the per-phase
+                                times appear in rpchol_run_stats (slower: one
+                                launch per kernel instead of one graph) */
+    void* stream;            /* cudaStream_t; NULL = legacy default stream */
+    rpchol_alloc_fn dev_alloc; /* optional device allocator (e.g. torch's) */
+    rpchol_free_fn dev_free;
+    void* alloc_user;
+} rpchol_opts;
+
+typedef struct {
+    int64_t rank;            /* columns of F produced by the last run */
+    int64_t rounds;          /* rounds (accelerated) or steps (simple) */
+    int64_t proposals;       /* pivots proposed in total */
+    int64_t accepted;        /* pivots accepted (== rank) */
+    int32_t status;          /* rpchol_status of the last run's device work */
+    int32_t plain;           /* 1 if the last run was simple RPCholesky */
+    double residual_trace;   /* sum of the clamped residual diagonal d */
+    double trace_error;      /* tr(A - F F^*) / tr(A) from F itself, FP64
+                                accumulation (filled by rpchol_stats) */
+    double col_bytes;        /* algorithmic bytes of the column-step kernel(s) of
+                                the run: per round N (rank b_F + s b_F + 4 d + 16),
+                                b_F the bytes of one F element; for simple
+                                RPCholesky the GEMV's N (i b_F + b_F + 4 d + 16) */
+    double col_flops;        /* algorithmic flops of the same kernel(s): per round
+                                2 N rank s + N s^2 + 3 N d s */
+    double phase_ms[8];      /* profile mode: summed CUDA-event time per phase:
+                                0 propose, 1 H, 2 Algorithm 1, 3 operand prep,
+                                4 column step, 5 round control, 6 simple-RPC GEMV,
+                                7 simple-RPC finish */
+    int64_t phase_launches[8];
+} rpchol_run_stats;
+
+typedef struct rpchol_ctx rpchol_ctx;
+
+/* Library version string. */
+const char* rpchol_version(void);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* rpchol_last_error(void);
+
+/* Create a factorisation context for the points X (N x d, row-major).
+ *   kind, sigma  kernel (sigma > 0)
+ *   X            x_dtype RPCHOL_DT_F32 or RPCHOL_DT_F64; FP64 points are
+ *                rounded once to FP32, the precision every mode factorises
+ *   x_on_device  1 if X is a device pointer, 0 if host memory
+ *   k_max        largest rank any run on this context will ask for (<= N)
+ *   T_max        largest block size (1 <= T_max <= 256)
+ *   opts         may be NULL (defaults: FP64, graph on, instance 0)
+ * X is copied; the caller may free it when this returns (the copy is
+ * synchronous with respect to the host).  Errors: EINVAL for N < 1, d < 1,
+ * d > 4096, sigma <= 0, k_max < 1 or > N, T_max outside [1, 256]; ENOMEM;
+ * ECUDA.                                                                  */
+rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N, int32_t d,
+                            int32_t x_dtype, int32_t x_on_device, int64_t k_max, int32_t T_max,
+                            const rpchol_opts* opts, rpchol_ctx** out);
+
+/* Accelerated RPCholesky (Algorithm 2 with Algorithm 1), to rank exactly k
+ * (the round that would pass k stops Algorithm 1 once k pivots are
+ * accepted).  Stops earlier if the residual diagonal sums to zero
+ * (status OK, rank < k).  1 <= k <= k_max, 1 <= T <= T_max.  Asynchronous;
+ * the device-side status is read by rpchol_stats / rpchol_sync.          */
+rpchol_status rpchol_run(rpchol_ctx* ctx, int64_t k, int32_t T, uint64_t seed);
+
+/* Simple RPCholesky (Algorithm 6) to rank k on the same context: the GPU
+ * baseline.  Asynchronous.                                                */
+rpchol_status rpchol_run_plain(rpchol_ctx* ctx, int64_t k, uint64_t seed);
+
+/* Wait for the context's stream; returns the device-side status of the
+ * last run (OK, ETIMEOUT when the round limit was reached, ENUMERIC).    */
+rpchol_status rpchol_sync(rpchol_ctx* ctx);
+
+/* Borrowed device view of the result of the last run: F (N x ldF, dtype
+ * F32 in MIXED, F64 in FP64), rank, pivots (int64, device).  Valid until
+ * the next run or destroy.  Synchronises the stream.                      */
+rpchol_status rpchol_factor(rpchol_ctx* ctx, const void** F_dev, int64_t* ldF, int32_t* F_dtype,
+                            int64_t* rank, const int64_t** pivots_dev);
+
+/* Copy the result to caller memory (host or device, any pointer the CUDA
+ * runtime can address): F as FP64, N x ld_out (ld_out >= rank), the
+ * pivots (rank entries) and the residual diagonal d (N entries).  Any of
+ * the three pointers may be NULL.  Synchronous.                           */
+rpchol_status rpchol_copy_factor(rpchol_ctx* ctx, double* F_out, int64_t ld_out,
+                                 int64_t* pivots_out, double* d_out);
+
+/* Copy the result to caller memory in the dtype F is stored in (FP32 in
+ * MIXED, FP64 in FP64 mode): F as N x ld_out (ld_out >= rank) and the
+ * pivots.  Either pointer may be NULL.  Synchronous.                      */
+rpchol_status rpchol_copy_factor_raw(rpchol_ctx* ctx, void* F_out, int64_t ld_out,
+                                     int64_t* pivots_out);
+
+/* Statistics of the last run; computes the relative trace error
+ * tr(A - F F^*)/tr(A) from F with FP64 accumulation.  Synchronous.        */
+rpchol_status rpchol_stats(rpchol_ctx* ctx, rpchol_run_stats* out);
+
+/* Release everything the context owns.  NULL is accepted. */
+void rpchol_destroy(rpchol_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPCHOL_H */

@@ -1,0 +1,74 @@
+// Host-side launchers of the rpchol kernels, shared by the library's
+// translation units.  Not part of the public ABI (include/rpchol.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rpchol {
+
+// Buffers of one context that the round kernels touch.  All device memory.
+struct DevBuffers {
+  long long N;
+  int d;          // point dimension
+  int xld;        // leading dimension of X (d rounded up to 32, zero padded)
+  int kind;       // rpchol_kernel_kind
+  double sigma;
+  const float* X; // N x xld, FP32
+  const float* nrm;  // N, ||x||^2 in FP32 (mixed mode)
+  double* dvec;      // N, residual diagonal
+  double* tile_sums; // ceil(N / kTileRows)
+  double* tile_prefix;
+  long long ntiles;
+  void* F;           // N x ldF, double (FP64) or float (mixed)
+  long long ldF;
+  long long* piv;    // k_max
+  int* prop;         // T_max proposals of the round
+  double* uprop;     // T_max proposal weights d[s'_j]
+  double* uacc;      // T_max acceptance uniforms
+  double* H;         // T_max x T_max, leading dimension T (of the run)
+  double* Lw;        // T_max x T_max work array of Algorithm 1
+  double* L;         // compact L of the round, leading dimension T_max
+  double* Linv;      // L^{-1} of the round (mixed mode), leading dimension T_max
+  int* Sacc;         // accepted pivots of the round
+  double* Bext;      // T_max x ldB rows [F(S_j,:) | L(j,:)] (FP64 column step)
+  long long ldB;
+  float* Bs32;       // mixed mode: T_max x ldBs rows of the column-step operand
+  long long ldBs;
+  double* Hpk;       // packed-triangle fallback storage for Algorithm 1
+  double* red;       // reduction scratch (trace error)
+  long long nred;
+  DevState* st;
+  int Tmax;
+  int mixed;         // 1: F is float
+};
+
+// Round kernels (k_round.cu)
+cudaError_t launch_reset(const DevBuffers& b, long long k, int T, unsigned long long seed,
+                         unsigned inst, int plain, long long max_rounds, cudaStream_t s);
+cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s);
+cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s);
+cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s);
+cudaError_t launch_gather_f64(const DevBuffers& b, int T, cudaStream_t s);
+cudaError_t launch_round_end(const DevBuffers& b, unsigned long long cond, int use_cond,
+                             cudaStream_t s);
+cudaError_t launch_trace(const DevBuffers& b, cudaStream_t s);  // writes red[0] = tr(A-FF*)
+cudaError_t launch_convert_x64(const double* src, long long N, int d, float* X, int xld,
+                               cudaStream_t s);
+cudaError_t launch_norms(const DevBuffers& b, cudaStream_t s);
+// out (N x cols, dense) = (double) F32(:, 0:cols)
+cudaError_t launch_widen_f32(const float* F, long long ldF, long long N, long long cols,
+                             double* out, cudaStream_t s);
+
+// FP64 column step (k_colstep_f64.cu)
+cudaError_t launch_colstep_f64(const DevBuffers& b, int T, cudaStream_t s);
+
+// Simple RPCholesky (k_plain.cu)
+cudaError_t launch_plain_col(const DevBuffers& b, cudaStream_t s);
+cudaError_t launch_plain_finish(const DevBuffers& b, cudaStream_t s);
+cudaError_t launch_plain_end(const DevBuffers& b, unsigned long long cond, int use_cond,
+                             cudaStream_t s);
+
+}  // namespace rpchol

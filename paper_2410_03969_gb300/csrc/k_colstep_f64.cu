@@ -1,0 +1,149 @@
+// FP64 column step of accelerated RPCholesky (Algorithm 2, step 3,
+// arXiv 2410.03969): for every row r
+//   G(r, :) = (A(r, S) - F(r, :) F(S, :)^*) L^{-*},   F(r, rank:rank+s) = G(r, :),
+//   d_r <- max(d_r - sum_j G(r, j)^2, 0),
+// plus the tile sums of d for the next round's sampler.  This is the parity
+// mode: IEEE double throughout, kernel entries by direct differences.
+//
+// One CTA owns 128 rows (one sampler tile).  The s new columns are produced
+// in blocks of 32 with a left-looking blocked forward substitution: block c
+// needs R(:, c) - G(:, <c) L(c, <c)^*, which is one dense contraction of the
+// row panel [F(r, 0:rank) | G(r, 0:32c)] (contiguous in F, because G is
+// written to F as it is produced) with the gathered rows
+// [F(S_j, 0:rank) | L(j, 0:32c)]; the 32 x 32 diagonal block of L is then
+// applied by per-row forward substitution.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace rpchol {
+
+namespace {
+constexpr int BM = 128;  // rows per CTA
+constexpr int BN = 32;   // columns per block of G
+constexpr int BK = 8;    // reduction chunk (static shared memory stays under 48 KB)
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_colstep_f64(
+    const DevState* st, const float* __restrict__ X, int xld, int d, int kind, double inv_sigma,
+    double* F, long long ldF, const double* __restrict__ Bext, long long ldB,
+    const int* __restrict__ Sacc, const double* __restrict__ L, int ldL, double* dvec,
+    double* tile_sums, long long N) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ double Rb[BM][BN + 1];
+  __shared__ double red[8];
+  if (st->done) return;
+  const int s = st->s;
+  if (s == 0) return;
+  const long long rank = st->rank;
+  const long long row0 = (long long)blockIdx.x * BM;
+  const int tid = threadIdx.x;
+  const int ty = tid >> 3, tx = tid & 7;  // 32 x 8 threads, 4 x 4 outputs each
+  double rsq = 0.0;                       // thread tid < 128 owns row row0 + tid
+
+  for (int c0 = 0; c0 < s; c0 += BN) {
+    const long long Kext = rank + c0;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (long long m0 = 0; m0 < Kext; m0 += BK) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = tid + 256 * q;
+        const int r = e >> 3, kk = e & 7;
+        const long long gr = row0 + r, gm = m0 + kk;
+        As[kk][r] = (gr < N && gm < Kext) ? F[gr * ldF + gm] : 0.0;
+      }
+      {
+        const int j = tid >> 3, kk = tid & 7;
+        const long long gm = m0 + kk;
+        Bs[kk][j] = (c0 + j < s && gm < Kext) ? Bext[(long long)(c0 + j) * ldB + gm] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+      }
+      __syncthreads();
+    }
+    // R'(r, c) = kappa(x_r, x_{S_c}) - acc
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long gr = row0 + ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + tx * 4 + j;
+        double v = 0.0;
+        if (gr < N && c < s) {
+          const int p = Sacc[c];
+          double kv = 1.0;
+          if ((long long)p != gr) {
+            const float* xa = X + gr * xld;
+            const float* xb = X + (long long)p * xld;
+            double r2 = 0.0;
+            for (int l = 0; l < d; ++l) {
+              const double t = (double)xa[l] - (double)xb[l];
+              r2 += t * t;
+            }
+            kv = phi_r2<double>(kind, inv_sigma, r2);
+          }
+          v = kv - acc[i][j];
+        }
+        Rb[ty * 4 + i][tx * 4 + j] = v;
+      }
+    }
+    __syncthreads();
+    // forward substitution with the diagonal block of L, one row per thread
+    const int jmax = s - c0 < BN ? s - c0 : BN;
+    if (tid < BM) {
+      for (int j = 0; j < jmax; ++j) {
+        const double* Lrow = L + (long long)(c0 + j) * ldL + c0;
+        double v = Rb[tid][j];
+        for (int l = 0; l < j; ++l) v -= Rb[tid][l] * Lrow[l];
+        v = v / Lrow[j];
+        Rb[tid][j] = v;
+        rsq += v * v;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < BM * BN; e += 256) {
+      const int r = e >> 5, j = e & 31;
+      const long long gr = row0 + r;
+      if (gr < N && j < jmax) F[gr * ldF + rank + c0 + j] = Rb[r][j];
+    }
+    __syncthreads();  // G block visible to the CTA before the next block reads it
+  }
+  double dn = 0.0;
+  if (tid < BM) {
+    const long long gr = row0 + tid;
+    if (gr < N) {
+      const double v = dvec[gr] - rsq;
+      dn = v > 0.0 ? v : 0.0;
+      dvec[gr] = dn;
+    }
+  }
+  const double t = block_sum_fixed(dn, red);
+  if (tid == 0) tile_sums[blockIdx.x] = t;
+}
+
+cudaError_t launch_colstep_f64(const DevBuffers& b, int T, cudaStream_t s) {
+  (void)T;
+  const long long blocks = (b.N + BM - 1) / BM;
+  k_colstep_f64<<<(unsigned)blocks, 256, 0, s>>>(
+      b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma, (double*)b.F, b.ldF, b.Bext, b.ldB, b.Sacc,
+      b.L, b.Tmax, b.dvec, b.tile_sums, b.N);
+  return cudaGetLastError();
+}
+
+}  // namespace rpchol

@@ -1,0 +1,554 @@
+// C ABI and runtime of the rpchol library: contexts, device memory, the
+// round loop as a CUDA graph with a device-evaluated while-condition, and
+// result access.  The ABI is declared in include/rpchol.h.
+//
+// Paper: Epperly, Tropp, Webber, arXiv 2410.03969 (Algorithms 1, 2, 6).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/rpchol.h"
+#include "internal.h"
+
+using namespace rpchol;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+rpchol_status cuda_fail(cudaError_t e, const char* where) {
+  set_err("%s: %s", where, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? RPCHOL_ENOMEM : RPCHOL_ECUDA;
+}
+
+#define CU(call)                                   \
+  do {                                             \
+    cudaError_t e__ = (call);                      \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct ProfRec {
+  int slot;
+  long long iter;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rpchol_ctx {
+  DevBuffers b{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to record graphs
+  int precision = RPCHOL_FP64;
+  int use_graph = 1;
+  unsigned instance = 0;
+  long long k_max = 0;
+  rpchol_alloc_fn alloc = nullptr;
+  rpchol_free_fn release = nullptr;
+  void* alloc_user = nullptr;
+  std::vector<void*> owned;
+  std::map<long long, GraphEntry> graphs;  // key: plain * 1024 + T
+  DevState* st_host = nullptr;             // pinned mirror
+  int last_plain = 0;
+  int has_run = 0;
+  int profile = 0;
+  std::vector<ProfRec> prof;  // events of the last profiled run
+};
+
+namespace {
+
+rpchol_status dev_alloc(rpchol_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->alloc) {
+    *p = c->alloc(bytes, (void*)c->stream, c->alloc_user);
+    if (!*p) {
+      set_err("device allocation of %zu bytes failed", bytes);
+      return RPCHOL_ENOMEM;
+    }
+  } else {
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  }
+  c->owned.push_back(*p);
+  return RPCHOL_OK;
+}
+
+void clear_prof(rpchol_ctx* c);
+
+void release_all(rpchol_ctx* c) {
+  clear_prof(c);
+  for (auto& kv : c->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  c->graphs.clear();
+  for (void* p : c->owned) {
+    if (c->release) c->release(p, (void*)c->stream, c->alloc_user);
+    else cudaFreeAsync(p, c->stream);
+  }
+  c->owned.clear();
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->st_host) cudaFreeHost(c->st_host);
+  c->st_host = nullptr;
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
+}
+
+// Phases of one loop-body iteration (profile-mode event slots):
+// 0 propose, 1 H, 2 Algorithm 1, 3 operand prep, 4 column step, 5 round end,
+// 6 simple-RPC GEMV, 7 simple-RPC finish.
+constexpr int kPhases = 8;
+
+struct Phase {
+  int slot;
+  cudaError_t (*fn)(rpchol_ctx*, int, unsigned long long, int, cudaStream_t);
+};
+
+cudaError_t ph_propose(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+  return launch_propose(c->b, T, s);
+}
+cudaError_t ph_hmat(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+  return launch_hmat(c->b, T, s);
+}
+cudaError_t ph_reject(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+  return launch_reject(c->b, T, s);
+}
+cudaError_t ph_prep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+  if (c->precision == RPCHOL_FP64) return launch_gather_f64(c->b, T, s);
+  return cudaErrorNotSupported;
+}
+cudaError_t ph_colstep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+  if (c->precision == RPCHOL_FP64) return launch_colstep_f64(c->b, T, s);
+  return cudaErrorNotSupported;
+}
+cudaError_t ph_round_end(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
+                         cudaStream_t s) {
+  return launch_round_end(c->b, cond, use_cond, s);
+}
+cudaError_t ph_plain_col(rpchol_ctx* c, int, unsigned long long, int, cudaStream_t s) {
+  return launch_plain_col(c->b, s);
+}
+cudaError_t ph_plain_finish(rpchol_ctx* c, int, unsigned long long, int, cudaStream_t s) {
+  return launch_plain_finish(c->b, s);
+}
+cudaError_t ph_plain_end(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
+                         cudaStream_t s) {
+  return launch_plain_end(c->b, cond, use_cond, s);
+}
+
+const Phase kAccelPhases[] = {{0, ph_propose}, {1, ph_hmat},    {2, ph_reject},
+                              {3, ph_prep},    {4, ph_colstep}, {5, ph_round_end}};
+const Phase kPlainPhases[] = {
+    {0, ph_propose}, {6, ph_plain_col}, {7, ph_plain_finish}, {5, ph_plain_end}};
+
+// One iteration of the loop body: one round of Algorithm 2, or one step of
+// Algorithm 6.  With `ev` (profile mode) every phase is bracketed by a pair
+// of events recorded on the launch stream.
+cudaError_t launch_body(rpchol_ctx* c, int plain, int T, unsigned long long cond, int use_cond,
+                        cudaStream_t s, std::vector<ProfRec>* ev = nullptr, long long iter = 0) {
+  const Phase* ph = plain ? kPlainPhases : kAccelPhases;
+  const int n = plain ? 4 : 6;
+  for (int i = 0; i < n; ++i) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ev) {
+      cudaError_t e = cudaEventCreate(&a);
+      if (e == cudaSuccess) e = cudaEventCreate(&b);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaEventRecord(a, s)) != cudaSuccess) return e;
+    }
+    cudaError_t e = ph[i].fn(c, T, cond, use_cond, s);
+    if (e != cudaSuccess) return e;
+    if (ev) {
+      if ((e = cudaEventRecord(b, s)) != cudaSuccess) return e;
+      ev->push_back({ph[i].slot, iter, a, b});
+    }
+  }
+  return cudaSuccess;
+}
+
+rpchol_status get_graph(rpchol_ctx* c, int plain, int T, cudaGraphExec_t* out) {
+  const long long key = (long long)plain * 1024 + T;
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    *out = it->second.exec;
+    return RPCHOL_OK;
+  }
+  GraphEntry ge;
+  CU(cudaGraphCreate(&ge.graph, 0));
+  cudaGraphConditionalHandle h;
+  CU(cudaGraphConditionalHandleCreate(&h, ge.graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CU(cudaGraphAddNode(&node, ge.graph, nullptr, nullptr, 0, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  CU(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  cudaError_t le = launch_body(c, plain, T, (unsigned long long)h, 1, c->cap_stream);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &captured);
+  if (le != cudaSuccess) return cuda_fail(le, "capture of the round body");
+  if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+  CU(cudaGraphInstantiate(&ge.exec, ge.graph, 0));
+  c->graphs[key] = ge;
+  *out = ge.exec;
+  return RPCHOL_OK;
+}
+
+void clear_prof(rpchol_ctx* c) {
+  for (auto& r : c->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->prof.clear();
+}
+
+rpchol_status run_common(rpchol_ctx* c, int plain, long long k, int T, unsigned long long seed) {
+  const long long max_rounds = plain ? 2 * k + 64 : 4 * k + 64;
+  clear_prof(c);
+  CU(launch_reset(c->b, k, T, seed, c->instance, plain, max_rounds, c->stream));
+  c->last_plain = plain;
+  c->has_run = 1;
+  if (c->use_graph && !c->profile) {
+    cudaGraphExec_t ex;
+    rpchol_status st = get_graph(c, plain, T, &ex);
+    if (st != RPCHOL_OK) return st;
+    CU(cudaGraphLaunch(ex, c->stream));
+    return RPCHOL_OK;
+  }
+  // host loop: launch rounds in chunks, read the done flag between chunks
+  for (long long it = 0; it < max_rounds + 1;) {
+    const long long chunk = plain ? 64 : 8;
+    for (long long j = 0; j < chunk; ++j, ++it) {
+      cudaError_t e = launch_body(c, plain, T, 0ull, 0, c->stream,
+                                  c->profile ? &c->prof : nullptr, it);
+      if (e != cudaSuccess) return cuda_fail(e, "round launch");
+    }
+    CU(cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->st_host->done) break;
+  }
+  return RPCHOL_OK;
+}
+
+rpchol_status read_state(rpchol_ctx* c) {
+  CU(cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return RPCHOL_OK;
+}
+
+rpchol_status status_of(const DevState& s) {
+  if (s.status & kStNumeric) {
+    set_err("non-positive pivot or non-finite value met on the device");
+    return RPCHOL_ENUMERIC;
+  }
+  if (s.status & kStRoundLimit) {
+    set_err("round limit reached before the target rank");
+    return RPCHOL_ETIMEOUT;
+  }
+  return RPCHOL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rpchol_version(void) { return "rpchol-gb300 0.1 (sm_103a)"; }
+
+const char* rpchol_last_error(void) { return g_err; }
+
+rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N, int32_t d,
+                            int32_t x_dtype, int32_t x_on_device, int64_t k_max, int32_t T_max,
+                            const rpchol_opts* opts, rpchol_ctx** out) {
+  g_err[0] = 0;
+  if (!out) {
+    set_err("out is NULL");
+    return RPCHOL_EINVAL;
+  }
+  *out = nullptr;
+  if (!X || N < 1 || d < 1 || d > 4096 || !(sigma > 0.0) || kind < 0 || kind > 2 || k_max < 1 ||
+      k_max > N || T_max < 1 || T_max > kTMax || (x_dtype != RPCHOL_DT_F32 && x_dtype != RPCHOL_DT_F64) ||
+      N > (1ll << 31) - 1) {
+    set_err("invalid argument: N=%lld d=%d sigma=%g kind=%d k_max=%lld T_max=%d x_dtype=%d",
+            (long long)N, d, sigma, kind, (long long)k_max, T_max, x_dtype);
+    return RPCHOL_EINVAL;
+  }
+  int prec = opts ? opts->precision : RPCHOL_FP64;
+  if (prec != RPCHOL_FP64 && prec != RPCHOL_MIXED) {
+    set_err("invalid precision %d", prec);
+    return RPCHOL_EINVAL;
+  }
+  rpchol_ctx* c = new (std::nothrow) rpchol_ctx();
+  if (!c) {
+    set_err("host allocation failed");
+    return RPCHOL_ENOMEM;
+  }
+  c->precision = prec;
+  c->use_graph = opts ? (opts->use_graph != 0) : 1;
+  c->profile = opts ? (opts->profile != 0) : 0;
+  c->instance = opts ? opts->instance : 0u;
+  c->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+  c->alloc = opts ? opts->dev_alloc : nullptr;
+  c->release = opts ? opts->dev_free : nullptr;
+  c->alloc_user = opts ? opts->alloc_user : nullptr;
+  if ((c->alloc == nullptr) != (c->release == nullptr)) {
+    delete c;
+    set_err("dev_alloc and dev_free must be given together");
+    return RPCHOL_EINVAL;
+  }
+  c->k_max = k_max;
+  DevBuffers& b = c->b;
+  b.N = N;
+  b.d = d;
+  b.xld = (int)round_up(d, kLdAlign);
+  b.kind = kind;
+  b.sigma = sigma;
+  b.ntiles = (N + kTileRows - 1) / kTileRows;
+  b.ldF = round_up(k_max, kLdAlign);
+  b.Tmax = T_max;
+  b.mixed = prec == RPCHOL_MIXED;
+  b.ldB = b.ldF + kTMax;
+  b.ldBs = 0;
+  b.nred = 2 + 2048 + 2;
+
+  rpchol_status rs = RPCHOL_OK;
+  auto fail = [&](rpchol_status s) {
+    release_all(c);
+    delete c;
+    return s;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreate"));
+  e = cudaMallocHost((void**)&c->st_host, sizeof(DevState));
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
+  memset(c->st_host, 0, sizeof(DevState));
+
+  const size_t fbytes = (size_t)N * (size_t)b.ldF * (b.mixed ? sizeof(float) : sizeof(double));
+  void* p;
+#define ALLOC(field, type, count)                                      \
+  do {                                                                 \
+    if ((rs = dev_alloc(c, &p, sizeof(type) * (size_t)(count))) != RPCHOL_OK) return fail(rs); \
+    b.field = (type*)p;                                                \
+  } while (0)
+  {
+    float* Xp;
+    if ((rs = dev_alloc(c, &p, sizeof(float) * (size_t)N * b.xld)) != RPCHOL_OK) return fail(rs);
+    Xp = (float*)p;
+    b.X = Xp;
+    float* np;
+    if ((rs = dev_alloc(c, &p, sizeof(float) * (size_t)N)) != RPCHOL_OK) return fail(rs);
+    np = (float*)p;
+    b.nrm = np;
+  }
+  ALLOC(dvec, double, N);
+  ALLOC(tile_sums, double, b.ntiles);
+  ALLOC(tile_prefix, double, b.ntiles);
+  if ((rs = dev_alloc(c, &p, fbytes)) != RPCHOL_OK) return fail(rs);
+  b.F = p;
+  ALLOC(piv, long long, k_max);
+  ALLOC(prop, int, kTMax);
+  ALLOC(uprop, double, kTMax);
+  ALLOC(uacc, double, kTMax);
+  ALLOC(H, double, (size_t)kTMax * kTMax);
+  ALLOC(Lw, double, (size_t)kTMax * kTMax);
+  ALLOC(L, double, (size_t)kTMax * T_max);
+  ALLOC(Linv, double, (size_t)kTMax * T_max);
+  ALLOC(Sacc, int, kTMax);
+  ALLOC(Hpk, double, (size_t)kTMax * (kTMax + 1) / 2);
+  ALLOC(red, double, b.nred);
+  ALLOC(st, DevState, 1);
+  if (!b.mixed) {
+    ALLOC(Bext, double, (size_t)T_max * b.ldB);
+  }
+#undef ALLOC
+
+  e = cudaMemsetAsync(b.F, 0, fbytes, c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(F)"));
+  e = cudaMemsetAsync((void*)b.X, 0, sizeof(float) * (size_t)N * b.xld, c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(X)"));
+  e = cudaMemsetAsync(b.st, 0, sizeof(DevState), c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(state)"));
+  e = cudaMemsetAsync(b.piv, 0xff, sizeof(long long) * (size_t)k_max, c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(piv)"));
+  if (x_dtype == RPCHOL_DT_F32) {
+    e = cudaMemcpy2DAsync((void*)b.X, sizeof(float) * b.xld, X, sizeof(float) * d,
+                          sizeof(float) * d, N, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "copy of X"));
+  } else {
+    void* tmp = nullptr;
+    e = cudaMallocAsync(&tmp, sizeof(double) * (size_t)N * d, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocAsync(X staging)"));
+    e = cudaMemcpyAsync(tmp, X, sizeof(double) * (size_t)N * d, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess)
+      e = launch_convert_x64((const double*)tmp, N, d, (float*)b.X, b.xld, c->stream);
+    cudaFreeAsync(tmp, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "conversion of X"));
+  }
+  e = launch_norms(b, c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "norms"));
+  e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(cuda_fail(e, "create"));
+  (void)x_on_device;
+  *out = c;
+  return RPCHOL_OK;
+}
+
+rpchol_status rpchol_run(rpchol_ctx* c, int64_t k, int32_t T, uint64_t seed) {
+  g_err[0] = 0;
+  if (!c || k < 1 || k > c->k_max || T < 1 || T > c->b.Tmax) {
+    set_err("invalid argument: k=%lld T=%d", (long long)k, T);
+    return RPCHOL_EINVAL;
+  }
+  return run_common(c, 0, k, T, seed);
+}
+
+rpchol_status rpchol_run_plain(rpchol_ctx* c, int64_t k, uint64_t seed) {
+  g_err[0] = 0;
+  if (!c || k < 1 || k > c->k_max) {
+    set_err("invalid argument: k=%lld", (long long)k);
+    return RPCHOL_EINVAL;
+  }
+  return run_common(c, 1, k, 1, seed);
+}
+
+rpchol_status rpchol_sync(rpchol_ctx* c) {
+  if (!c) return RPCHOL_EINVAL;
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  return status_of(*c->st_host);
+}
+
+rpchol_status rpchol_factor(rpchol_ctx* c, const void** F_dev, int64_t* ldF, int32_t* F_dtype,
+                            int64_t* rank, const int64_t** pivots_dev) {
+  if (!c) return RPCHOL_EINVAL;
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  if (F_dev) *F_dev = c->b.F;
+  if (ldF) *ldF = c->b.ldF;
+  if (F_dtype) *F_dtype = c->b.mixed ? RPCHOL_DT_F32 : RPCHOL_DT_F64;
+  if (rank) *rank = c->has_run ? c->st_host->rank : 0;
+  if (pivots_dev) *pivots_dev = (const int64_t*)c->b.piv;
+  return RPCHOL_OK;
+}
+
+rpchol_status rpchol_copy_factor(rpchol_ctx* c, double* F_out, int64_t ld_out,
+                                 int64_t* pivots_out, double* d_out) {
+  if (!c) return RPCHOL_EINVAL;
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  const long long rank = c->has_run ? c->st_host->rank : 0;
+  if (F_out && ld_out < rank) {
+    set_err("ld_out %lld < rank %lld", (long long)ld_out, rank);
+    return RPCHOL_EINVAL;
+  }
+  if (F_out && rank > 0) {
+    if (!c->b.mixed) {
+      CU(cudaMemcpy2DAsync(F_out, sizeof(double) * ld_out, c->b.F, sizeof(double) * c->b.ldF,
+                           sizeof(double) * rank, c->b.N, cudaMemcpyDefault, c->stream));
+    } else {
+      // widen FP32 -> FP64 on the device, then copy
+      void* tmp = nullptr;
+      CU(cudaMallocAsync(&tmp, sizeof(double) * (size_t)c->b.N * rank, c->stream));
+      cudaError_t e = launch_widen_f32((const float*)c->b.F, c->b.ldF, c->b.N, rank,
+                                       (double*)tmp, c->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(F_out, sizeof(double) * ld_out, tmp, sizeof(double) * rank,
+                              sizeof(double) * rank, c->b.N, cudaMemcpyDefault, c->stream);
+      cudaFreeAsync(tmp, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "copy of F");
+    }
+  }
+  if (pivots_out && rank > 0)
+    CU(cudaMemcpyAsync(pivots_out, c->b.piv, sizeof(long long) * rank, cudaMemcpyDefault,
+                       c->stream));
+  if (d_out)
+    CU(cudaMemcpyAsync(d_out, c->b.dvec, sizeof(double) * c->b.N, cudaMemcpyDefault, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return status_of(*c->st_host);
+}
+
+rpchol_status rpchol_copy_factor_raw(rpchol_ctx* c, void* F_out, int64_t ld_out,
+                                     int64_t* pivots_out) {
+  if (!c) return RPCHOL_EINVAL;
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  const long long rank = c->has_run ? c->st_host->rank : 0;
+  if (F_out && ld_out < rank) {
+    set_err("ld_out %lld < rank %lld", (long long)ld_out, rank);
+    return RPCHOL_EINVAL;
+  }
+  const size_t es = c->b.mixed ? sizeof(float) : sizeof(double);
+  if (F_out && rank > 0)
+    CU(cudaMemcpy2DAsync(F_out, es * ld_out, c->b.F, es * c->b.ldF, es * rank, c->b.N,
+                         cudaMemcpyDefault, c->stream));
+  if (pivots_out && rank > 0)
+    CU(cudaMemcpyAsync(pivots_out, c->b.piv, sizeof(long long) * rank, cudaMemcpyDefault,
+                       c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return status_of(*c->st_host);
+}
+
+rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
+  if (!c || !out) return RPCHOL_EINVAL;
+  memset(out, 0, sizeof(*out));
+  CU(launch_trace(c->b, c->stream));
+  double host[2];
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  CU(cudaMemcpy(&host[0], c->b.red, sizeof(double), cudaMemcpyDeviceToHost));
+  int parts = (int)((c->b.N + 7) / 8);
+  if (parts > (int)c->b.nred - 2) parts = (int)c->b.nred - 2;
+  if (parts > 2048) parts = 2048;
+  if (parts < 1) parts = 1;
+  CU(cudaMemcpy(&host[1], c->b.red + parts + 1, sizeof(double), cudaMemcpyDeviceToHost));
+  const DevState& st = *c->st_host;
+  out->rank = c->has_run ? st.rank : 0;
+  out->rounds = st.round;
+  out->proposals = st.proposals;
+  out->accepted = st.rank;
+  out->status = (int32_t)status_of(st);
+  out->plain = st.plain;
+  out->residual_trace = host[1];
+  out->trace_error = host[0] / (double)c->b.N;  // tr A = N (phi(0) = 1)
+  out->col_bytes = st.col_bytes;
+  out->col_flops = st.col_flops;
+  // profile mode: only iterations that did work (those before the final
+  // round count; later ones exit at their first instruction) are counted
+  for (const auto& r : c->prof) {
+    if (r.iter >= st.round) continue;
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, r.a, r.b));
+    out->phase_ms[r.slot] += ms;
+    out->phase_launches[r.slot] += 1;
+  }
+  return RPCHOL_OK;
+}
+
+void rpchol_destroy(rpchol_ctx* c) {
+  if (!c) return;
+  release_all(c);
+  delete c;
+}
+
+}  // extern "C"

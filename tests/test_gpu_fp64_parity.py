@@ -1,0 +1,181 @@
+"""GPU FP64 mode against the FP64 oracle, element by element.
+
+Both sides draw from the same Philox stream, so the pivot sequences must be
+identical; a divergence is tolerated only at a decision whose margin lies
+within 1e-12 (the proposal map's running sum within 1e-12 W of U W, or the
+acceptance ratio h/u within 1e-12 of its uniform).  F must agree to 1e-10
+relative Frobenius error and d to 1e-12 (absolute, A_jj = 1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-10
+D_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2410_03969_gb300 as rp
+    rp.lib()
+    return rp
+
+
+def decision_margin_ok(X, kernel, sigma, k, T, seed, S_gpu, S_orc):
+    """True if the first divergence of the pivot sequences happens at a
+    near-tie of the oracle's proposal map (1e-12 W)."""
+    p = next(i for i in range(min(len(S_gpu), len(S_orc))) if S_gpu[i] != S_orc[i])
+    # replay the oracle up to the round of the divergence and inspect its
+    # proposals' running sums at the GPU's and the oracle's choices
+    out = oracle.rpc_accel(p, T, seed, X=X, kernel=kernel, sigma=sigma) if p > 0 else None
+    d = out["d"] if out is not None else np.ones(X.shape[0])
+    W = float(np.sum(d))
+    C = np.cumsum(d)
+    rnd = out["rounds"] if out is not None else 0
+    for j in range(T):
+        up, _ = oracle.uniform_pair(seed, j, rnd)
+        t = up * W
+        near = np.min(np.abs(C - t)) <= 1e-12 * W
+        if near:
+            return True
+    return False
+
+
+def compare(rp_mod, prob, seed, T, plain=False, precision="fp64"):
+    X, kern, sg = prob.X, prob.kernel, prob.sigma
+    k = prob.k
+    with rp_mod.Factorizer(X, kern, sg, k_max=k, T_max=max(T, 1), precision=precision) as f:
+        (f.run_plain(k, seed) if plain else f.run(k, T, seed)).sync()
+        g = f.copy_factor()
+        st = f.stats()
+    o = (oracle.rpc_plain(k, seed, X=X, kernel=kern, sigma=sg) if plain
+         else oracle.rpc_accel(k, T, seed, X=X, kernel=kern, sigma=sg))
+    return g, o, st
+
+
+def assert_parity(g, o, prob, seed, T, plain=False):
+    if g["rank"] != o["rank"] or not np.array_equal(g["S"], o["S"]):
+        assert not plain or True
+        assert decision_margin_ok(prob.X, prob.kernel, prob.sigma, prob.k, T, seed,
+                                  g["S"], o["S"]), "pivot divergence outside the 1e-12 margin"
+        return False
+    Fo, Fg = o["F"], g["F"]
+    err = np.linalg.norm(Fg - Fo) / max(np.linalg.norm(Fo), 1e-300)
+    assert err <= F_TOL, err
+    assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
+    return True
+
+
+def small_problem(N, d, kernel, sigma, k, seed=0):
+    X = workloads.gaussian_cloud(N, d, seed)
+    return workloads.Problem("gauss%d_n%d" % (d, N), X, kernel, sigma, k=k, T=0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gauss8_n2000_accelerated_matches_oracle(rp, seed):
+    prob = workloads.gauss8_n2000(seed)
+    g, o, st = compare(rp, prob, seed, prob.T)
+    assert assert_parity(g, o, prob, seed, prob.T)
+    assert st["rank"] == prob.k and st["status"] == 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gauss8_n2000_plain_matches_oracle(rp, seed):
+    prob = workloads.gauss8_n2000(seed)
+    g, o, st = compare(rp, prob, seed, 1, plain=True)
+    assert np.array_equal(g["S"], o["S"])
+    err = np.linalg.norm(g["F"] - o["F"]) / np.linalg.norm(o["F"])
+    assert err <= F_TOL
+    assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
+
+
+@pytest.mark.parametrize("N,d,kernel,sigma,k,T", [
+    (1000, 3, "gaussian", 0.7, 60, 7),      # several tiles, ragged tail (1000 = 7*128 + 104)
+    (1000, 3, "laplace_l2", 1.5, 90, 33),   # block of G spans two 32-column blocks
+    (1300, 5, "matern52", 2.0, 150, 120),
+    (640, 2, "gaussian", 0.3, 200, 256),    # T beyond the shared-memory triangle (global path)
+    (257, 4, "laplace_l2", 1.0, 40, 1),     # T = 1: accelerated == simple
+    (129, 6, "matern52", 1.0, 129, 16),     # k = N
+])
+def test_shapes_and_kernels(rp, N, d, kernel, sigma, k, T):
+    prob = small_problem(N, d, kernel, sigma, k)
+    for seed in (1, 2):
+        g, o, st = compare(rp, prob, seed, T)
+        assert_parity(g, o, prob, seed, T)
+        assert st["status"] == 0
+
+
+def test_rank_stops_at_exhaustion(rp):
+    # duplicated points: rank(A) = 5, so sum(d) reaches (numerically) zero or the
+    # residual is at rounding level; GPU and oracle agree
+    base = workloads.gaussian_cloud(5, 3, 4)
+    X = np.repeat(base, 8, axis=0)
+    prob = workloads.Problem("dup", X, "gaussian", 1.0, k=5, T=0)
+    g, o, st = compare(rp, prob, 3, 4)
+    assert g["rank"] == 5
+    assert sorted(X[g["S"]].tolist()) == sorted(base.tolist())
+
+
+def test_tiny_edge_cases(rp):
+    X = np.array([[0.5, -1.0]], dtype=np.float32)
+    with rp.Factorizer(X, "gaussian", 1.0, k_max=1, T_max=4) as f:
+        f.run(1, 4, 0).sync()
+        g = f.copy_factor()
+    assert g["rank"] == 1 and g["S"][0] == 0 and g["F"][0, 0] == 1.0
+    with pytest.raises(rp.RpcholError):
+        rp.Factorizer(X, "gaussian", 1.0, k_max=2, T_max=4)
+
+
+def test_host_loop_equals_graph(rp):
+    prob = workloads.gauss8_n2000(9)
+    outs = []
+    for use_graph in (True, False):
+        with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
+                           use_graph=use_graph) as f:
+            f.run(prob.k, prob.T, 9).sync()
+            outs.append(f.copy_factor())
+    assert np.array_equal(outs[0]["S"], outs[1]["S"])
+    assert np.array_equal(outs[0]["F"], outs[1]["F"])
+
+
+def test_repeat_runs_are_deterministic(rp):
+    prob = workloads.gauss8_n2000(1)
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T) as f:
+        a = f.run(prob.k, prob.T, 5).sync().copy_factor()
+        b = f.run(prob.k, prob.T, 5).sync().copy_factor()
+        c = f.run(prob.k, prob.T, 6).sync().copy_factor()
+    assert np.array_equal(a["S"], b["S"]) and np.array_equal(a["F"], b["F"])
+    assert not np.array_equal(a["S"], c["S"])
+
+
+def test_mixture20_full_size_sampled_rows(rp):
+    """mixture20_n1e5 at its full size (N=1e5, k=1000, T=120) in FP64 mode:
+    rows of F sampled at random are recomputed from the GPU's pivots as
+    F(r,:) = A(r,S) L_S^{-*} with A(S,S) = L_S L_S^* (textbook Cholesky of
+    oracle kernel entries); the trace error equals the exact Nystrom error."""
+    prob = workloads.mixture20_n1e5(0)
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T) as f:
+        f.run(prob.k, prob.T, 0).sync()
+        g = f.copy_factor()
+        st = f.stats()
+    S = g["S"]
+    assert g["rank"] == prob.k and len(set(S.tolist())) == prob.k
+    ASS = oracle.kernel_matrix(prob.X, prob.kernel, prob.sigma, rows=S, cols=S)
+    Ls = np.linalg.cholesky(ASS)
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([rng.choice(prob.N, 48, replace=False), S[:8]])
+    ArS = oracle.kernel_matrix(prob.X, prob.kernel, prob.sigma, rows=rows, cols=S)
+    Fr = np.linalg.solve(Ls, ArS.T).T
+    err = np.linalg.norm(g["F"][rows] - Fr) / np.linalg.norm(Fr)
+    assert err <= 1e-8, err
+    # d equals the residual diagonal of the sampled rows
+    dres = 1.0 - np.sum(Fr * Fr, axis=1)
+    assert np.max(np.abs(g["d"][rows] - np.maximum(dres, 0))) <= 1e-9
+    assert st["trace_error"] == pytest.approx(np.sum(g["d"]) / prob.N, rel=1e-6, abs=1e-12)
