@@ -1,0 +1,388 @@
+"""Benchmark: time-to-rank-k and pivots/s of accelerated RPCholesky on GB300.
+
+One step = one complete factorisation of the workload's kernel matrix to
+rank k (every round of Algorithm 2: proposals, H, Algorithm 1, fused column
+step, diagonal update) with a fresh seed, inputs resident in HBM.  The
+default workload is mixture20_n1e5 (N = 1e5, d = 20, 10-component Gaussian
+mixture, Gaussian kernel with the median bandwidth of 1000 pairs, k = 1000,
+T = 120).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision mixed|fp64]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload.  With N > 1 (one
+process per GPU under torch.distributed.run) every rank factorises its own
+seeds independently (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "time-to-rank-k & pivots/s vs plain RPCholesky, 1 GB300, equal trace error; p99"
+UNIT = "pivots/s"
+
+
+def _pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    i = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))
+    return v[i]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(prob, budget_s=12.0, threads=None):
+    """Time the FP64 oracle (accelerated RPCholesky, as it stands) on the first
+    N' points of the workload, to rank k; the time scales linearly in N at
+    fixed k, so the full-size estimate is t * N / N'."""
+    import oracle
+    oracle.build()
+    cores = threads or os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    N = prob.N
+    Np = max(prob.k * 2, min(N, 20000))
+    # calibrate on a small sample, then size the measured one to the budget
+    Nc = max(prob.k + 1, min(Np, 4000))
+    t0 = time.perf_counter()
+    oracle.rpc_accel(prob.k, prob.T, 0, X=prob.X[:Nc], kernel=prob.kernel, sigma=prob.sigma)
+    tc = time.perf_counter() - t0
+    Np = int(min(N, max(Nc, Nc * budget_s / max(tc, 1e-3))))
+    t0 = time.perf_counter()
+    out = oracle.rpc_accel(prob.k, prob.T, 0, X=prob.X[:Np], kernel=prob.kernel, sigma=prob.sigma)
+    t = time.perf_counter() - t0
+    est = t * N / Np
+    return {"value": prob.k / est, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "FP64 C oracle, accelerated RPCholesky to rank %d on the first %d of %d "
+                      "points (%.1f s); time scaled by N/N' = %.2f to %.1f s per factorisation"
+                      % (prob.k, Np, N, t, N / Np, est),
+            "seconds_sample": t, "seconds_full_estimate": est, "rank": out["rank"]}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob = workloads.WORKLOADS[args.workload](0)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    used = oracle.set_threads(cores)
+    Np = min(prob.N, max(2 * prob.k, prob.N // 20))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.rpc_accel(prob.k, prob.T, 1000 + i, X=prob.X[:Np], kernel=prob.kernel,
+                         sigma=prob.sigma)
+        t = (time.perf_counter() - t0) * prob.N / Np
+        if i >= args.warmup:
+            times.append(t)
+    mean = sum(times) / len(times)
+    value = prob.k / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": prob.name, "N": prob.N, "d": prob.d, "k": prob.k, "T": prob.T,
+                   "kernel": prob.kernel, "sigma": prob.sigma},
+        "time_to_rank_k_ms": {"p50": _pct(times, 50) * 1e3, "p99": _pct(times, 99) * 1e3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": "each step: FP64 C oracle, accelerated RPCholesky to rank "
+                                   "%d on the first %d of %d points, time scaled by N/N'"
+                                   % (prob.k, Np, prob.N)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def ours_arm(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2410_03969_gb300 as rp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    rp.lib()
+    prob = workloads.WORKLOADS[args.workload](0)
+    k, T = prob.k, prob.T
+    prec = args.precision
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    Xd = torch.from_numpy(prob.X).cuda()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    f = rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=k, T_max=T, precision=prec)
+    seed_base = 1000 * (rank + 1)
+    for i in range(args.warmup):
+        f.run(k, T, seed_base + 900 + i)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K factorisations, per-step CUDA events, L2 flushed between steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    rounds = []
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            f.run(k, T, seed_base + i)
+            evs[i][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    # per-step trace error and round counts (re-run the same seeds, outside timing)
+    terr, accepted_rate = [], []
+    for i in range(min(args.steps, 5)):
+        f.run(k, T, seed_base + i)
+        st = f.stats()
+        terr.append(st["trace_error"])
+        rounds.append(st["rounds"])
+        accepted_rate.append(st["accepted"] / max(1, st["proposals"]))
+    st_last = f.stats()
+    mean_rounds = sum(rounds) / len(rounds)
+    launches = int(round(args.steps * (1 + 6 * mean_rounds)))
+
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps * k / (total_ms / 1e3)
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # ---- simple RPCholesky on the same GPU, same precision (the baseline)
+        pm, pterr = [], []
+        for i in range(args.plain_steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.run_plain(k, seed_base + i)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pm.append(a.elapsed_time(b))
+            pterr.append(f.stats()["trace_error"])
+        extra["plain_gpu"] = {
+            "ms_p50": _pct(pm, 50), "pivots_per_s": k / (statistics.median(pm) / 1e3),
+            "trace_error_mean": sum(pterr) / len(pterr), "steps": len(pm), "precision": prec}
+        extra["speedup_vs_plain_gpu"] = statistics.median(pm) / statistics.median(step_ms)
+        extra["trace_error_ratio_vs_plain_gpu"] = (sum(terr) / len(terr)) / (
+            sum(pterr) / len(pterr))
+        # ---- other precision mode, for context
+        other = "fp64" if prec == "mixed" else None
+        if other:
+            with rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=k, T_max=T,
+                               precision=other) as g:
+                om, ot = [], []
+                for i in range(2):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+                        enable_timing=True)
+                    a.record(stream)
+                    g.run(k, T, seed_base + i)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    om.append(a.elapsed_time(b))
+                    ot.append(g.stats()["trace_error"])
+            extra["fp64_mode"] = {"ms_p50": _pct(om, 50), "trace_error_mean": sum(ot) / len(ot)}
+
+        # ---- roofline of the dominant kernel: profiled pass (per-kernel events)
+        peaks, src = _peaks()
+        with rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=k, T_max=T, precision=prec,
+                           profile=True) as g:
+            g.run(k, T, seed_base)
+            sp = g.stats()
+        col_ms = sp["phase_ms"]["colstep"]
+        nl = max(1, sp["phase_launches"]["colstep"])
+        phase_total = sum(sp["phase_ms"].values())
+        if prec == "fp64":
+            achieved = sp["col_flops"] / (col_ms / 1e3) / 1e12
+            peak = args.fp64_peak
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "FP64 FMA rate measured on this GB300 by a probe "
+                                   "(%.2f TFLOP/s); 'of measured'" % peak}
+        else:
+            achieved = sp["col_bytes"] / (col_ms / 1e3) / 1e9
+            peak = peaks["hbm_gbs"]
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "hbm_gbs of MEASURED_PEAKS.json (%s)" % src}
+        roof.update({"kernel": "column step", "launches": nl, "avg_launch_ms": col_ms / nl,
+                     "alg_bytes_per_launch": sp["col_bytes"] / nl,
+                     "alg_flops_per_launch": sp["col_flops"] / nl,
+                     "share_of_profiled_step": col_ms / max(phase_total, 1e-9),
+                     "phase_ms": sp["phase_ms"]})
+        extra["roofline"] = roof
+
+        # ---- end to end through the public API with host buffers
+        Xh = torch.from_numpy(prob.X).pin_memory()
+        es = 4 if prec == "mixed" else 8
+        Fh = torch.empty((prob.N, k), dtype=torch.float32 if es == 4 else torch.float64,
+                         pin_memory=True)
+        Ph = torch.empty(k, dtype=torch.int64, pin_memory=True)
+        em = []
+        for i in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with rp.Factorizer(Xh, prob.kernel, prob.sigma, k_max=k, T_max=T,
+                               precision=prec) as g:
+                g.run(k, T, seed_base + i)
+                g.copy_factor_raw(Fh.data_ptr(), k, Ph.data_ptr())
+            em.append(time.perf_counter() - t0)
+        e2e_t = statistics.median(em)
+        extra["e2e"] = {"value": k / e2e_t, "unit": UNIT, "ms_p50": e2e_t * 1e3,
+                        "h2d_bytes_per_step": int(prob.X.nbytes),
+                        "d2h_bytes_per_step": int(prob.N * k * es + k * 8),
+                        "path": "rpchol_create from pinned host X, rpchol_run, "
+                                "rpchol_copy_factor_raw to pinned host F and pivots, destroy"}
+        if not args.no_cpu_baseline:
+            extra["cpu_baseline"] = oracle_sample(prob, budget_s=args.cpu_budget)
+    f.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3/f32+f64" if prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": prob.name, "N": prob.N, "d": prob.d, "k": k, "T": T,
+                       "kernel": prob.kernel, "sigma": prob.sigma, "precision": prec,
+                       "l2": "flushed between steps (256 MiB write, outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_rank_k_ms": {"p50": _pct(step_ms, 50), "p99": _pct(step_ms, 99),
+                                  "mean": statistics.mean(step_ms),
+                                  "min": min(step_ms), "max": max(step_ms)},
+            "trace_error": {"mean": statistics.mean(terr),
+                            "sd": statistics.pstdev(terr) if len(terr) > 1 else 0.0},
+            "rounds_mean": mean_rounds,
+            "acceptance_rate": statistics.mean(accepted_rate),
+            "wall_s_timed_region": t_wall,
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "status": st_last["status"],
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixture20_n1e5", choices=list(workloads.WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="timed region only")
+    ap.add_argument("--fp64-peak", type=float, default=1.194,
+                    help="FP64 FMA peak (TFLOP/s) measured on GB300 by an FMA-loop probe")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

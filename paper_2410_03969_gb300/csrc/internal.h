@@ -62,8 +62,9 @@ cudaError_t launch_norms(const DevBuffers& b, cudaStream_t s);
 cudaError_t launch_widen_f32(const float* F, long long ldF, long long N, long long cols,
                              double* out, cudaStream_t s);
 
-// FP64 column step (k_colstep_f64.cu)
+// CUDA-core column steps (k_colstep_simt.cu): FP64, and FP32 for mixed mode
 cudaError_t launch_colstep_f64(const DevBuffers& b, int T, cudaStream_t s);
+cudaError_t launch_colstep_f32_simt(const DevBuffers& b, int T, cudaStream_t s);
 
 // Simple RPCholesky (k_plain.cu)
 cudaError_t launch_plain_col(const DevBuffers& b, cudaStream_t s);

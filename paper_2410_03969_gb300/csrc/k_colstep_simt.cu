@@ -1,4 +1,4 @@
-// FP64 column step of accelerated RPCholesky (Algorithm 2, step 3,
+// CUDA-core column step of accelerated RPCholesky (Algorithm 2, step 3,
 // arXiv 2410.03969): for every row r
 //   G(r, :) = (A(r, S) - F(r, :) F(S, :)^*) L^{-*},   F(r, rank:rank+s) = G(r, :),
 //   d_r <- max(d_r - sum_j G(r, j)^2, 0),
@@ -24,14 +24,18 @@ constexpr int BN = 32;   // columns per block of G
 constexpr int BK = 8;    // reduction chunk (static shared memory stays under 48 KB)
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_colstep_f64(
+// TR = double: the FP64 parity mode.  TR = float: the CUDA-core FP32 path of
+// mixed mode (F in FP32, FP32 FMA with FP32 accumulation; L is rounded to
+// FP32; d stays FP64 and the squared row norms are accumulated in FP64).
+template <typename TR>
+__global__ void __launch_bounds__(256) k_colstep_simt(
     const DevState* st, const float* __restrict__ X, int xld, int d, int kind, double inv_sigma,
-    double* F, long long ldF, const double* __restrict__ Bext, long long ldB,
+    TR* F, long long ldF, const TR* __restrict__ Bext, long long ldB,
     const int* __restrict__ Sacc, const double* __restrict__ L, int ldL, double* dvec,
     double* tile_sums, long long N) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
-  __shared__ double Rb[BM][BN + 1];
+  __shared__ TR As[BK][BM + 1];
+  __shared__ TR Bs[BK][BN + 1];
+  __shared__ TR Rb[BM][BN + 1];
   __shared__ double red[8];
   if (st->done) return;
   const int s = st->s;
@@ -44,28 +48,28 @@ __global__ void __launch_bounds__(256) k_colstep_f64(
 
   for (int c0 = 0; c0 < s; c0 += BN) {
     const long long Kext = rank + c0;
-    double acc[4][4];
+    TR acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < 4; ++j) acc[i][j] = (TR)0;
     for (long long m0 = 0; m0 < Kext; m0 += BK) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int e = tid + 256 * q;
         const int r = e >> 3, kk = e & 7;
         const long long gr = row0 + r, gm = m0 + kk;
-        As[kk][r] = (gr < N && gm < Kext) ? F[gr * ldF + gm] : 0.0;
+        As[kk][r] = (gr < N && gm < Kext) ? F[gr * ldF + gm] : (TR)0;
       }
       {
         const int j = tid >> 3, kk = tid & 7;
         const long long gm = m0 + kk;
-        Bs[kk][j] = (c0 + j < s && gm < Kext) ? Bext[(long long)(c0 + j) * ldB + gm] : 0.0;
+        Bs[kk][j] = (c0 + j < s && gm < Kext) ? Bext[(long long)(c0 + j) * ldB + gm] : (TR)0;
       }
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        double a[4], b[4];
+        TR a[4], b[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
@@ -84,19 +88,19 @@ __global__ void __launch_bounds__(256) k_colstep_f64(
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = c0 + tx * 4 + j;
-        double v = 0.0;
+        TR v = (TR)0;
         if (gr < N && c < s) {
           const int p = Sacc[c];
-          double kv = 1.0;
+          TR kv = (TR)1;
           if ((long long)p != gr) {
             const float* xa = X + gr * xld;
             const float* xb = X + (long long)p * xld;
-            double r2 = 0.0;
+            TR r2 = (TR)0;
             for (int l = 0; l < d; ++l) {
-              const double t = (double)xa[l] - (double)xb[l];
+              const TR t = (TR)xa[l] - (TR)xb[l];
               r2 += t * t;
             }
-            kv = phi_r2<double>(kind, inv_sigma, r2);
+            kv = phi_r2<TR>(kind, (TR)inv_sigma, r2);
           }
           v = kv - acc[i][j];
         }
@@ -109,11 +113,11 @@ __global__ void __launch_bounds__(256) k_colstep_f64(
     if (tid < BM) {
       for (int j = 0; j < jmax; ++j) {
         const double* Lrow = L + (long long)(c0 + j) * ldL + c0;
-        double v = Rb[tid][j];
-        for (int l = 0; l < j; ++l) v -= Rb[tid][l] * Lrow[l];
-        v = v / Lrow[j];
+        TR v = Rb[tid][j];
+        for (int l = 0; l < j; ++l) v -= Rb[tid][l] * (TR)Lrow[l];
+        v = v / (TR)Lrow[j];
         Rb[tid][j] = v;
-        rsq += v * v;
+        rsq += (double)v * (double)v;
       }
     }
     __syncthreads();
@@ -140,9 +144,18 @@ __global__ void __launch_bounds__(256) k_colstep_f64(
 cudaError_t launch_colstep_f64(const DevBuffers& b, int T, cudaStream_t s) {
   (void)T;
   const long long blocks = (b.N + BM - 1) / BM;
-  k_colstep_f64<<<(unsigned)blocks, 256, 0, s>>>(
+  k_colstep_simt<double><<<(unsigned)blocks, 256, 0, s>>>(
       b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma, (double*)b.F, b.ldF, b.Bext, b.ldB, b.Sacc,
       b.L, b.Tmax, b.dvec, b.tile_sums, b.N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colstep_f32_simt(const DevBuffers& b, int T, cudaStream_t s) {
+  (void)T;
+  const long long blocks = (b.N + BM - 1) / BM;
+  k_colstep_simt<float><<<(unsigned)blocks, 256, 0, s>>>(
+      b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma, (float*)b.F, b.ldF, (const float*)b.Bext,
+      b.ldB, b.Sacc, b.L, b.Tmax, b.dvec, b.tile_sums, b.N);
   return cudaGetLastError();
 }
 

@@ -310,11 +310,12 @@ cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ gather
-// Rows of the extended operand of the FP64 column step:
+// Rows of the extended operand of the CUDA-core column step:
 //   Bext(j, m) = F(S_j, m) for m < rank,  L(j, m - rank) for rank <= m < rank + s.
-__global__ void k_gather_f64(const DevState* st, const double* __restrict__ F, long long ldF,
+template <typename TR>
+__global__ void k_gather_ext(const DevState* st, const TR* __restrict__ F, long long ldF,
                              const int* __restrict__ Sacc, const double* __restrict__ L, int ldL,
-                             double* Bext, long long ldB) {
+                             TR* Bext, long long ldB) {
   if (st->done) return;
   const int s = st->s;
   const int j = blockIdx.x;
@@ -323,12 +324,16 @@ __global__ void k_gather_f64(const DevState* st, const double* __restrict__ F, l
   const long long src = (long long)Sacc[j] * ldF;
   for (long long m = threadIdx.x; m < rank + s; m += blockDim.x)
     Bext[(long long)j * ldB + m] =
-        m < rank ? F[src + m] : L[(long long)j * ldL + (m - rank)];
+        m < rank ? F[src + m] : (TR)L[(long long)j * ldL + (m - rank)];
 }
 
 cudaError_t launch_gather_f64(const DevBuffers& b, int T, cudaStream_t s) {
-  k_gather_f64<<<T, 256, 0, s>>>(b.st, (const double*)b.F, b.ldF, b.Sacc, b.L, b.Tmax, b.Bext,
-                                 b.ldB);
+  if (b.mixed)
+    k_gather_ext<float><<<T, 256, 0, s>>>(b.st, (const float*)b.F, b.ldF, b.Sacc, b.L, b.Tmax,
+                                          (float*)b.Bext, b.ldB);
+  else
+    k_gather_ext<double><<<T, 256, 0, s>>>(b.st, (const double*)b.F, b.ldF, b.Sacc, b.L, b.Tmax,
+                                           b.Bext, b.ldB);
   return cudaGetLastError();
 }
 

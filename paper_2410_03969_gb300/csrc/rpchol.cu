@@ -133,12 +133,11 @@ cudaError_t ph_reject(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_
   return launch_reject(c->b, T, s);
 }
 cudaError_t ph_prep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
-  if (c->precision == RPCHOL_FP64) return launch_gather_f64(c->b, T, s);
-  return cudaErrorNotSupported;
+  return launch_gather_f64(c->b, T, s);
 }
 cudaError_t ph_colstep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
   if (c->precision == RPCHOL_FP64) return launch_colstep_f64(c->b, T, s);
-  return cudaErrorNotSupported;
+  return launch_colstep_f32_simt(c->b, T, s);
 }
 cudaError_t ph_round_end(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
                          cudaStream_t s) {
@@ -378,9 +377,7 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   ALLOC(Hpk, double, (size_t)kTMax * (kTMax + 1) / 2);
   ALLOC(red, double, b.nred);
   ALLOC(st, DevState, 1);
-  if (!b.mixed) {
-    ALLOC(Bext, double, (size_t)T_max * b.ldB);
-  }
+  ALLOC(Bext, double, (size_t)T_max * b.ldB);  // float rows in mixed mode
 #undef ALLOC
 
   e = cudaMemsetAsync(b.F, 0, fbytes, c->stream);
