@@ -45,6 +45,9 @@ struct DevBuffers {
   int mixed;         // 1: F is float
 };
 
+// Thread-local message returned by rpchol_last_error (rpchol.cu).
+void set_last_error(const char* fmt, ...);
+
 // Round kernels (k_round.cu)
 cudaError_t launch_reset(const DevBuffers& b, long long k, int T, unsigned long long seed,
                          unsigned inst, int plain, long long max_rounds, cudaStream_t s);

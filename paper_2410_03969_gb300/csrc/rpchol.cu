@@ -28,6 +28,17 @@ void set_err(const char* fmt, ...) {
   va_end(ap);
 }
 
+}  // namespace
+
+void rpchol::set_last_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+
 rpchol_status cuda_fail(cudaError_t e, const char* where) {
   set_err("%s: %s", where, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? RPCHOL_ENOMEM : RPCHOL_ECUDA;
