@@ -177,6 +177,30 @@ rpchol_status rpchol_copy_factor_raw(rpchol_ctx* ctx, void* F_out, int64_t ld_ou
  * tr(A - F F^*)/tr(A) from F with FP64 accumulation.  Synchronous.        */
 rpchol_status rpchol_stats(rpchol_ctx* ctx, rpchol_run_stats* out);
 
+/* Relative trace error tr(A - F F^*) / tr(A) of a caller-provided factor,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * serves callers that cannot allocate device memory at all, such as code
+ * inside a host runtime that reserves all device memory up front in its own
+ * pool and forbids cudaMalloc outside it, or a latency-critical loop where
+ * an allocation could block or fail.  It computes what rpchol_stats reports
+ * as trace_error, for any factor.
+ *   F_dev    device pointer, row-major N x ldF, dtype RPCHOL_DT_F32 or
+ *            RPCHOL_DT_F64; only columns 0..rank-1 are read (diag A = 1)
+ *   out_dev  device (or device-accessible) pointer to one double
+ *   stream   cudaStream_t (NULL = legacy default stream); asynchronous
+ * Scratch: per-tile partial sums in a static device array of 65,536 doubles
+ * (512 KiB) that every GPU loading the library keeps until the process
+ * exits; N > 8,388,608 is rejected with RPCHOL_EINVAL.  The first call on a
+ * device looks up the array's address on that device (make it before any
+ * stream capture on that device).  All calls share the array: calls whose
+ * kernels overlap on the GPU race, so serialise them.  Each call overwrites
+ * every partial it uses, so no state carries over between calls.
+ * Errors: EINVAL (null pointer, N < 1, rank < 0, ldF < rank, bad dtype,
+ * N too large), ECUDA.  Calls no allocator of any kind.                    */
+rpchol_status rpchol_trace_error_noalloc(const void* F_dev, int32_t F_dtype, int64_t N,
+                                         int64_t ldF, int64_t rank, double* out_dev,
+                                         void* stream);
+
 /* Release everything the context owns.  NULL is accepted. */
 void rpchol_destroy(rpchol_ctx* ctx);
 
