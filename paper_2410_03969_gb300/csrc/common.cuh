@@ -20,6 +20,7 @@ constexpr int kLdAlign = 32;
 enum StatusBits : int {
   kStRoundLimit = 1,   // round limit reached before rank k
   kStNumeric = 2,      // non-finite / non-positive pivot
+  kStTimeout = 4,      // a bounded device-side wait expired
 };
 
 // Run state, one per context, in device memory.  Written only by

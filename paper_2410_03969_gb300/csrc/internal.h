@@ -2,12 +2,34 @@
 // translation units.  Not part of the public ABI (include/rpchol.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "common.cuh"
 
 namespace rpchol {
+
+// Tensor maps and buffers of the tensor-core column step (mixed mode).
+struct TcMaps {
+  CUtensorMap F;        // F, box 32 x 128
+  CUtensorMap X, Xlo;   // TF32 head / tail planes of X, box 32 x 128
+  CUtensorMap FSh, FSl; // head / tail of F(S,:), box 32 x 64
+  CUtensorMap XSh, XSl; // head / tail of X_S, box 32 x 64
+  float* Xhp;
+  float* Xlp;
+  float* FShp;
+  float* FSlp;
+  float* XShp;
+  float* XSlp;
+  float* nrmS;          // 256
+  float* Linv32;        // 256 x 256
+  int* err;             // status word of the run state
+};
+
+cudaError_t launch_prep_tc(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
+cudaError_t launch_split_x(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
+cudaError_t launch_colstep_tc(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
 
 // Buffers of one context that the round kernels touch.  All device memory.
 struct DevBuffers {

@@ -7,6 +7,8 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -81,6 +83,8 @@ struct rpchol_ctx {
   int has_run = 0;
   int profile = 0;
   std::vector<ProfRec> prof;  // events of the last profiled run
+  int use_tc = 0;             // mixed mode: tensor-core column step
+  TcMaps tc{};
 };
 
 namespace {
@@ -124,6 +128,49 @@ void release_all(rpchol_ctx* c) {
   c->cap_stream = nullptr;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2-D fp32 map over a row-major (rows x inner) array with leading dimension
+// `inner`, box 32 (128 bytes) x box_rows, 128-byte swizzle, zero fill.
+rpchol_status make_map(CUtensorMap* m, const void* base, unsigned long long inner,
+                       unsigned long long rows, unsigned box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    set_err("cuTensorMapEncodeTiled is unavailable");
+    return RPCHOL_ECUDA;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 4ull};
+  cuuint32_t box[2] = {32u, box_rows};
+  cuuint32_t es[2] = {1u, 1u};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_err("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return RPCHOL_ECUDA;
+  }
+  return RPCHOL_OK;
+}
+
 // Phases of one loop-body iteration (profile-mode event slots):
 // 0 propose, 1 H, 2 Algorithm 1, 3 operand prep, 4 column step, 5 round end,
 // 6 simple-RPC GEMV, 7 simple-RPC finish.
@@ -144,10 +191,12 @@ cudaError_t ph_reject(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_
   return launch_reject(c->b, T, s);
 }
 cudaError_t ph_prep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+  if (c->use_tc) return launch_prep_tc(c->tc, c->b, s);
   return launch_gather_f64(c->b, T, s);
 }
 cudaError_t ph_colstep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
   if (c->precision == RPCHOL_FP64) return launch_colstep_f64(c->b, T, s);
+  if (c->use_tc) return launch_colstep_tc(c->tc, c->b, s);
   return launch_colstep_f32_simt(c->b, T, s);
 }
 cudaError_t ph_round_end(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
@@ -269,6 +318,10 @@ rpchol_status read_state(rpchol_ctx* c) {
 }
 
 rpchol_status status_of(const DevState& s) {
+  if (s.status & kStTimeout) {
+    set_err("a bounded device-side wait expired (tensor-core column step)");
+    return RPCHOL_ETIMEOUT;
+  }
   if (s.status & kStNumeric) {
     set_err("non-positive pivot or non-finite value met on the device");
     return RPCHOL_ENUMERIC;
@@ -415,6 +468,50 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   }
   e = launch_norms(b, c->stream);
   if (e != cudaSuccess) return fail(cuda_fail(e, "norms"));
+  if (b.mixed) {
+    // tensor-core column step: needs at least one full 128-row tile; the
+    // CUDA-core FP32 path serves smaller problems (and RPCHOL_COLSTEP=simt)
+    const char* env = getenv("RPCHOL_COLSTEP");
+    c->use_tc = (N >= 128) && !(env && strcmp(env, "simt") == 0);
+  }
+  if (c->use_tc) {
+    TcMaps& m = c->tc;
+    const size_t xbytes = sizeof(float) * (size_t)N * b.xld;
+    const size_t fsbytes = sizeof(float) * (size_t)kTMax * b.ldF;
+    const size_t xsbytes = sizeof(float) * (size_t)kTMax * b.xld;
+    void* q;
+    if ((rs = dev_alloc(c, &q, xbytes)) != RPCHOL_OK) return fail(rs);
+    m.Xhp = (float*)q;
+    if ((rs = dev_alloc(c, &q, xbytes)) != RPCHOL_OK) return fail(rs);
+    m.Xlp = (float*)q;
+    if ((rs = dev_alloc(c, &q, fsbytes)) != RPCHOL_OK) return fail(rs);
+    m.FShp = (float*)q;
+    if ((rs = dev_alloc(c, &q, fsbytes)) != RPCHOL_OK) return fail(rs);
+    m.FSlp = (float*)q;
+    if ((rs = dev_alloc(c, &q, xsbytes)) != RPCHOL_OK) return fail(rs);
+    m.XShp = (float*)q;
+    if ((rs = dev_alloc(c, &q, xsbytes)) != RPCHOL_OK) return fail(rs);
+    m.XSlp = (float*)q;
+    if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax)) != RPCHOL_OK) return fail(rs);
+    m.nrmS = (float*)q;
+    if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax * kTMax)) != RPCHOL_OK) return fail(rs);
+    m.Linv32 = (float*)q;
+    m.err = (int*)((char*)b.st + offsetof(DevState, status));
+    e = cudaMemsetAsync(m.FShp, 0, fsbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.FSlp, 0, fsbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.XShp, 0, xsbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.XSlp, 0, xsbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.Linv32, 0, sizeof(float) * kTMax * kTMax, c->stream);
+    if (e == cudaSuccess) e = launch_split_x(m, b, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "tensor-core operand setup"));
+    if ((rs = make_map(&m.F, b.F, b.ldF, N, 128)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.X, m.Xhp, b.xld, N, 128)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.Xlo, m.Xlp, b.xld, N, 128)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.FSh, m.FShp, b.ldF, kTMax, 64)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.FSl, m.FSlp, b.ldF, kTMax, 64)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.XSh, m.XShp, b.xld, kTMax, 64)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.XSl, m.XSlp, b.xld, kTMax, 64)) != RPCHOL_OK) return fail(rs);
+  }
   e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_fail(e, "create"));
   (void)x_on_device;

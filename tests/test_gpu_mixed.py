@@ -69,6 +69,56 @@ def test_mixed_mode_against_oracle(rp, name, make, T):
     assert abs(ratio - 1.0) <= 0.05, ratio
 
 
+@pytest.mark.parametrize("N,d,kernel,sigma,T", [
+    (1000, 3, "gaussian", 0.8, 16),        # ragged last tile (1000 = 7*128 + 104)
+    (4097, 20, "gaussian", 5.0, 120),      # one row in the last tile
+    (3000, 64, "laplace_l2", 3.0, 200),    # two K chunks for the distances
+    (2048, 70, "matern52", 8.0, 256),      # three K chunks, s_pad up to 256
+    (700, 8, "laplace_l2", 1.0, 40),
+])
+def test_first_round_column_step_matches_oracle(rp, N, d, kernel, sigma, T):
+    """Round 0 sees no FP32 factor yet, so its pivots are the oracle's; the
+    tensor-core column step (distances and G = R L^{-*}) must then reproduce
+    the oracle's FP64 columns to FP32-level accuracy."""
+    X = workloads.gaussian_cloud(N, d, 11)
+    o = oracle.rpc_accel(N, T, 7, X=X, kernel=kernel, sigma=sigma, max_rounds=1)
+    s0 = o["rank"]
+    with rp.Factorizer(X, kernel, sigma, k_max=s0, T_max=T, precision="mixed") as f:
+        f.run(s0, T, 7).sync()
+        g = f.copy_factor()
+        st = f.stats()
+    assert st["status"] == 0 and g["rank"] == s0 and st["rounds"] == 1
+    assert np.array_equal(g["S"], o["S"])
+    err = np.linalg.norm(g["F"] - o["F"]) / np.linalg.norm(o["F"])
+    assert err <= 2e-5, err
+    assert np.max(np.abs(g["d"] - o["d"])) <= 2e-5
+
+
+def test_high_rank_smooth_kernel(rp):
+    """Rank 1000 on the 10-component mixture with the median bandwidth (a
+    smooth kernel whose residual falls to ~3e-4 of tr A): late rounds work at
+    the precision floor of the mixed contractions.  The factor must stay a
+    valid Nystrom factor (row norms <= 1) and the trace error must match
+    simple RPCholesky's (FP64 oracle) within 5%."""
+    prob = workloads.mixture20_n1e5(0, N=4096)
+    k, T = 1000, 120
+    te, tp = [], []
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=k, T_max=T,
+                       precision="mixed") as f:
+        for seed in range(3):
+            f.run(k, T, seed).sync()
+            st = f.stats()
+            g = f.copy_factor(F=True, pivots=True, d=False)
+            assert st["status"] == 0 and st["rank"] == k
+            assert len(set(g["S"].tolist())) == k, "a pivot was chosen twice"
+            assert np.max(np.sum(g["F"] ** 2, axis=1)) <= 1.0 + 1e-4
+            te.append(st["trace_error"])
+            o = oracle.rpc_plain(k, seed, X=prob.X, kernel=prob.kernel, sigma=prob.sigma)
+            tp.append(np.sum(o["d"]) / prob.N)
+    ratio = np.mean(te) / np.mean(tp)
+    assert abs(ratio - 1.0) <= 0.05, (ratio, te, tp)
+
+
 def test_mixed_plain_baseline(rp):
     prob = workloads.gauss8_n2000(1)
     with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
