@@ -201,7 +201,8 @@ def ours_arm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    f = rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=k, T_max=T, precision=prec)
+    f = rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=k, T_max=T, precision=prec,
+                      use_graph=not args.no_graph)
     seed_base = 1000 * (rank + 1)
     for i in range(args.warmup):
         f.run(k, T, seed_base + 900 + i)
@@ -376,6 +377,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed region only")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven round loop (one launch per kernel), e.g. for ncu")
     ap.add_argument("--fp64-peak", type=float, default=1.194,
                     help="FP64 FMA peak (TFLOP/s) measured on GB300 by an FMA-loop probe")
     args = ap.parse_args()

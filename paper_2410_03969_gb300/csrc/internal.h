@@ -23,8 +23,10 @@ struct TcMaps {
   float* XShp;
   float* XSlp;
   float* nrmS;          // 256
-  float* Linv32;        // 256 x 256
+  float* Linv32;        // 256 x 256: the round's L in FP32 (lower triangle)
+  float* invd;          // 256: 1 / L(j,j)
   int* err;             // status word of the run state
+  int num_sms;          // persistent grid size of the column step
 };
 
 cudaError_t launch_prep_tc(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);

@@ -5,8 +5,8 @@
 //     columns [rank, 32 * ceil(rank / 32)) are zero so that padded MMA
 //     columns and padded K chunks contribute nothing;
 //   - ||x_{S_j}||^2;
-//   - L^{-1} of the round's compact Cholesky factor, by forward substitution
-//     in FP64 (one column per CTA), rounded once to FP32.
+//   - the blocked-substitution operand W built from the round's compact
+//     Cholesky factor L in FP64 and rounded once to FP32 (k_wblk below).
 // Also the one-time split of X into head and tail planes.
 #include <cuda_runtime.h>
 
@@ -63,30 +63,52 @@ __global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float
   }
 }
 
-// Column c of L^{-1}: solve L x = e_c (L lower triangular, s x s, FP64).
-__global__ void __launch_bounds__(32) k_linv(const DevState* st, const double* __restrict__ L,
-                                             int ldL, float* Linv32) {
-  __shared__ double x[kTMax];
+// Blocked forward substitution operand for G L^* = R.  With the columns in
+// blocks of 16 (block b covers columns j0 = 16 b .. j0 + 15) and D_b the
+// 16 x 16 diagonal block of L, block b of G is
+//   G_b = D_b^{-1} (R_b - G_{<j0} L(b, <j0)^*)
+//       = sum_{l < j0} G(:, l) W_b(l, :) + sum_{m < 16} R(:, j0 + m) W_b(j0 + m, :)
+// with W_b(l, jj) = -(D_b^{-1} L(b, <j0))(jj, l) for l < j0 and
+// W_b(j0 + m, jj) = D_b^{-1}(jj, m).  All of it is formed here in FP64 from
+// the FP64 L of Algorithm 1 and rounded once to FP32.  Block b occupies
+// (j0 + 16) x 16 floats at offset 256 b (b + 1) / 2, row l contiguous.
+// Rows and columns of L beyond s are taken as the identity, so padded
+// columns of G are copies of the (zero) padded columns of R.
+__global__ void __launch_bounds__(256) k_wblk(const DevState* st, const double* __restrict__ L,
+                                              int ldL, float* W) {
+  __shared__ double Dinv[16][17];
+  __shared__ double Lb[16][kTMax];  // rows j0..j0+15 of L, columns < j0
   if (st->done) return;
   const int s = st->s;
-  const int c = blockIdx.x;
-  if (c >= s) return;
-  const int lane = threadIdx.x;
-  for (int j = lane; j < c; j += 32) Linv32[(long long)j * 256 + c] = 0.f;
-  if (lane == 0) x[c] = 1.0 / L[(long long)c * ldL + c];
-  __syncwarp();
-  if (lane == 0) Linv32[(long long)c * 256 + c] = (float)x[c];
-  for (int j = c + 1; j < s; ++j) {
-    const double* Lr = L + (long long)j * ldL;
-    double acc = 0.0;
-    for (int l = c + lane; l < j; l += 32) acc += Lr[l] * x[l];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const double v = -acc / Lr[j];
-      x[j] = v;
-      Linv32[(long long)j * 256 + c] = (float)v;
+  const int b = blockIdx.x;
+  const int j0 = 16 * b;
+  if (j0 >= s) return;
+  const int t = threadIdx.x;
+  auto Lat = [&](int r, int c) -> double {  // L with identity padding beyond s
+    if (r >= s || c >= s) return r == c ? 1.0 : 0.0;
+    return c <= r ? L[(long long)r * ldL + c] : 0.0;
+  };
+  for (int e = t; e < 16 * j0; e += blockDim.x) Lb[e / j0][e % j0] = Lat(j0 + e / j0, e % j0);
+  // D_b^{-1} column m by forward substitution (16 threads)
+  if (t < 16) {
+    const int m = t;
+    for (int r = 0; r < 16; ++r) {
+      double v = (r == m) ? 1.0 : 0.0;
+      for (int c = m; c < r; ++c) v -= Lat(j0 + r, j0 + c) * Dinv[c][m];
+      Dinv[r][m] = r >= m ? v / Lat(j0 + r, j0 + r) : 0.0;
     }
-    __syncwarp();
+  }
+  __syncthreads();
+  float* Wb = W + 256 * (long long)b * (b + 1) / 2;
+  for (int e = t; e < 16 * j0; e += blockDim.x) {  // W_b(l, jj), l < j0
+    const int l = e >> 4, jj = e & 15;
+    double acc = 0.0;
+    for (int m = 0; m <= jj; ++m) acc += Dinv[jj][m] * Lb[m][l];
+    Wb[(long long)l * 16 + jj] = (float)(-acc);
+  }
+  for (int e = t; e < 256; e += blockDim.x) {  // W_b(j0 + m, jj) = D_b^{-1}(jj, m)
+    const int m = e >> 4, jj = e & 15;
+    Wb[(long long)(j0 + m) * 16 + jj] = (float)Dinv[jj][m];
   }
 }
 
@@ -102,7 +124,7 @@ __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, f
 cudaError_t launch_prep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
   k_prep_tc<<<kTMax, 256, 0, s>>>(b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc,
                                   m.FShp, m.FSlp, m.XShp, m.XSlp, m.nrmS);
-  k_linv<<<kTMax, 32, 0, s>>>(b.st, b.L, b.Tmax, m.Linv32);
+  k_wblk<<<kTMax / 16, 256, 0, s>>>(b.st, b.L, b.Tmax, m.Linv32);
   return cudaGetLastError();
 }
 

@@ -74,12 +74,14 @@ __global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __
                                                   const double* __restrict__ tile_sums,
                                                   double* tile_prefix, long long ntiles,
                                                   long long N, int* prop, double* uprop,
-                                                  double* uacc) {
+                                                  double* uacc, int use_smem) {
+  extern __shared__ double pref_smem[];
   __shared__ double wsum[32];
   __shared__ double carry_sh;
   if (st->done) return;
   const int T = st->T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* P = use_smem ? pref_smem : tile_prefix;  // inclusive prefix of the tile sums
   double run = 0.0;
   for (long long base = 0; base < ntiles; base += 1024) {
     const long long t = base + tid;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __
     }
     __syncthreads();
     incl += wsum[warp];
-    if (t < ntiles) tile_prefix[t] = run + incl;
+    if (t < ntiles) P[t] = run + incl;
     const double chunk = carry_sh;
     __syncthreads();
     run += chunk;
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __
     if (!(W > 0.0)) st->done = 1;
   }
   if (!(W > 0.0)) return;
-  __syncthreads();  // tile_prefix complete and visible to the CTA
+  __syncthreads();  // prefix complete and visible to the CTA
 
   const unsigned long long seed = st->seed;
   const unsigned round = (unsigned)st->round;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __
     long long lo = 0, hi = ntiles;
     while (lo < hi) {
       const long long mid = (lo + hi) >> 1;
-      if (tile_prefix[mid] > target) hi = mid;
+      if (P[mid] > target) hi = mid;
       else lo = mid + 1;
     }
     long long t = lo;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __
     }
     const long long r0 = t * kTileRows;
     const long long r1 = r0 + kTileRows < N ? r0 + kTileRows : N;
-    double running = t > 0 ? tile_prefix[t - 1] : 0.0;
+    double running = t > 0 ? P[t - 1] : 0.0;
     long long found = -1, last_pos = -1;
     for (long long c = r0; c < r1; c += 32) {
       const long long r = c + lane;
@@ -162,41 +164,61 @@ __global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __
 
 cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s) {
   (void)T;
-  k_propose<<<1, 1024, 0, s>>>(b.st, b.dvec, b.tile_sums, b.tile_prefix, b.ntiles, b.N, b.prop,
-                               b.uprop, b.uacc);
+  // the tile prefix lives in shared memory up to 20,480 tiles (N <= 2.6M)
+  const size_t bytes = (size_t)b.ntiles * sizeof(double);
+  const int use_smem = bytes <= 160 * 1024 ? 1 : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_propose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         160 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_propose<<<1, 1024, use_smem ? bytes : 0, s>>>(b.st, b.dvec, b.tile_sums, b.tile_prefix,
+                                                  b.ntiles, b.N, b.prop, b.uprop, b.uacc,
+                                                  use_smem);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ H
 // H = A(S',S') - F(S',:) F(S',:)^*, FP64 (FP32 factors are widened; their
 // products are exact in FP64).  Kernel entries by direct differences.
+// 8 x 8 output tiles, lower-triangle tiles only (H is symmetric; both
+// halves are written from the same value), F rows staged 32 columns at a
+// time.
 template <typename TF>
-__global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* __restrict__ X,
-                                              int xld, int d, int kind, double inv_sigma,
-                                              const TF* __restrict__ F, long long ldF,
-                                              const int* __restrict__ prop, double* H) {
-  __shared__ double Fa[16][17];
-  __shared__ double Fb[16][17];
+__global__ void __launch_bounds__(64) k_hmat(const DevState* st, const float* __restrict__ X,
+                                             int xld, int d, int kind, double inv_sigma,
+                                             const TF* __restrict__ F, long long ldF,
+                                             const int* __restrict__ prop, double* H) {
+  __shared__ double Fa[8][33];
+  __shared__ double Fb[8][33];
   if (st->done) return;
+  if (blockIdx.x > blockIdx.y) return;
   const int T = st->T;
   const long long rank = st->rank;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int a0 = blockIdx.y * 16, b0 = blockIdx.x * 16;
-  if (a0 >= T || b0 >= T) return;
-  const int ra = a0 + ty < T ? prop[a0 + ty] : prop[0];  // row loaded into Fa[ty]
-  const int rb = b0 + ty < T ? prop[b0 + ty] : prop[0];  // row loaded into Fb[ty]
+  const int a0 = blockIdx.y * 8, b0 = blockIdx.x * 8;
+  if (a0 >= T) return;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
   double acc = 0.0;
-  for (long long m0 = 0; m0 < rank; m0 += 16) {
-    const long long m = m0 + tx;
-    Fa[ty][tx] = m < rank ? (double)F[(long long)ra * ldF + m] : 0.0;
-    Fb[ty][tx] = m < rank ? (double)F[(long long)rb * ldF + m] : 0.0;
-    __syncthreads();
+  for (long long m0 = 0; m0 < rank; m0 += 32) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc += Fa[ty][q] * Fb[tx][q];
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + 64 * q;  // 0..255: row e >> 5, column e & 31
+      const int r = e >> 5, cc = e & 31;
+      const long long m = m0 + cc;
+      const int ra = a0 + r < T ? prop[a0 + r] : prop[0];
+      const int rb = b0 + r < T ? prop[b0 + r] : prop[0];
+      Fa[r][cc] = m < rank ? (double)F[(long long)ra * ldF + m] : 0.0;
+      Fb[r][cc] = m < rank ? (double)F[(long long)rb * ldF + m] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) acc += Fa[ty][q] * Fb[tx][q];
     __syncthreads();
   }
   const int a = a0 + ty, bcol = b0 + tx;
-  if (a < T && bcol < T) {
+  if (a < T && bcol < T && bcol <= a) {
     const int pa = prop[a], pb = prop[bcol];
     double kv = 1.0;
     if (pa != pb) {
@@ -209,19 +231,21 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
       }
       kv = phi_r2<double>(kind, inv_sigma, r2);
     }
-    H[(long long)a * T + bcol] = kv - acc;
+    const double h = kv - acc;
+    H[(long long)a * T + bcol] = h;
+    H[(long long)bcol * T + a] = h;
   }
 }
 
 cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s) {
-  const int nb = (T + 15) / 16;
+  const int nb = (T + 7) / 8;
   dim3 grid(nb, nb);
   if (b.mixed)
-    k_hmat<float><<<grid, 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
-                                       (const float*)b.F, b.ldF, b.prop, b.H);
+    k_hmat<float><<<grid, 64, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
+                                      (const float*)b.F, b.ldF, b.prop, b.H);
   else
-    k_hmat<double><<<grid, 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
-                                        (const double*)b.F, b.ldF, b.prop, b.H);
+    k_hmat<double><<<grid, 64, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
+                                       (const double*)b.F, b.ldF, b.prop, b.H);
   return cudaGetLastError();
 }
 
@@ -261,9 +285,9 @@ __global__ void __launch_bounds__(512) k_reject(DevState* st, const double* __re
     if (n >= maxacc) break;
     const double h = Hp[pk(i, i)];
     if (us[i] < h) {
-      const double pivv = sqrt(h);
+      const double inv = 1.0 / sqrt(h);
       for (int j = i + tid; j < T; j += nt) {
-        const double v = Hp[pk(j, i)] / pivv;
+        const double v = Hp[pk(j, i)] * inv;
         lc[j] = v;
         Lw[(long long)j * kTMax + n] = v;
       }

@@ -496,7 +496,17 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
     m.nrmS = (float*)q;
     if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax * kTMax)) != RPCHOL_OK) return fail(rs);
     m.Linv32 = (float*)q;
+    if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax)) != RPCHOL_OK) return fail(rs);
+    m.invd = (float*)q;
     m.err = (int*)((char*)b.st + offsetof(DevState, status));
+    {
+      int dev = 0, nsm = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          nsm < 1)
+        nsm = 148;
+      m.num_sms = nsm;
+    }
     e = cudaMemsetAsync(m.FShp, 0, fsbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.FSlp, 0, fsbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.XShp, 0, xsbytes, c->stream);

@@ -67,18 +67,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Wait for the phase with the given parity to complete, giving up at the
 // deadline (ns of %globaltimer) or when *abort is set.  Returns true when the
-// phase completed.
+// phase completed.  After every 16 failed polls the thread checks the abort
+// flag and the clock and backs off briefly.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   unsigned long long deadline,
                                                   volatile int* abort) {
-  for (;;) {
+  for (uint32_t n = 0;; ++n) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*abort) return false;
-    if (globaltimer_ns() > deadline) {
-      *abort = 1;
-      return false;
+    if ((n & 15) == 15) {
+      if (*abort) return false;
+      if (globaltimer_ns() > deadline) {
+        *abort = 1;
+        return false;
+      }
+      __nanosleep(64);
     }
   }
+}
+
+// Warp-wide bounded wait: lane 0 polls, the result is broadcast.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity,
+                                               unsigned long long deadline,
+                                               volatile int* abort) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity, deadline, abort) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  return ok != 0;
+}
+
+// One arrival per warp, by lane 0 after __syncwarp has ordered the warp's
+// prior shared-memory writes.
+__device__ __forceinline__ void mbar_arrive_warp(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
 }
 
 // ---------------------------------------------------------------- TMA
@@ -93,6 +114,23 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)map) : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy (L2 only), with group commit
+// and wait.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)),
+               "l"((unsigned long long)gmem)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // ---------------------------------------------------------------- TMEM
