@@ -112,6 +112,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _problem(args):
+    """The workload; --n-points shrinks N (small cases for profiling only)."""
+    make = workloads.WORKLOADS[args.workload]
+    return make(0, N=args.n_points) if args.n_points else make(0)
+
+
 def oracle_sample(prob, budget_s=12.0, threads=None):
     """Time the FP64 oracle (accelerated RPCholesky, as it stands) on the first
     N' points of the workload, to rank k; the time scales linearly in N at
@@ -143,7 +149,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    prob = workloads.WORKLOADS[args.workload](0)
+    prob = _problem(args)
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -189,7 +195,7 @@ def ours_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     rp.lib()
-    prob = workloads.WORKLOADS[args.workload](0)
+    prob = _problem(args)
     k, T = prob.k, prob.T
     prec = args.precision
     stream = torch.cuda.current_stream()
@@ -225,16 +231,17 @@ def ours_arm(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     # per-step trace error and round counts (re-run the same seeds, outside timing)
-    terr, accepted_rate = [], []
+    terr, accepted_rate, kl = [], [], []
     for i in range(min(args.steps, 5)):
         f.run(k, T, seed_base + i)
         st = f.stats()
         terr.append(st["trace_error"])
         rounds.append(st["rounds"])
+        kl.append(st["kernel_launches"])
         accepted_rate.append(st["accepted"] / max(1, st["proposals"]))
     st_last = f.stats()
     mean_rounds = sum(rounds) / len(rounds)
-    launches = int(round(args.steps * (1 + 6 * mean_rounds)))
+    launches = int(round(args.steps * sum(kl) / len(kl)))
 
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -371,12 +378,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixture20_n1e5", choices=list(workloads.WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed region only")
+    ap.add_argument("--n-points", type=int, default=0,
+                    help="override N of the workload (small profiling cases; not a bench line)")
     ap.add_argument("--no-graph", action="store_true",
                     help="host-driven round loop (one launch per kernel), e.g. for ncu")
     ap.add_argument("--fp64-peak", type=float, default=1.194,

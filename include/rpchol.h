@@ -113,6 +113,8 @@ typedef struct {
                                 4 column step, 5 round control, 6 simple-RPC GEMV,
                                 7 simple-RPC finish */
     int64_t phase_launches[8];
+    int64_t kernel_launches; /* kernels the last run launched on the device (the
+                                reset kernel plus every kernel of every loop body) */
 } rpchol_run_stats;
 
 typedef struct rpchol_ctx rpchol_ctx;

@@ -39,7 +39,8 @@ class RunStats(ctypes.Structure):
                 ("status", ctypes.c_int32), ("plain", ctypes.c_int32),
                 ("residual_trace", ctypes.c_double), ("trace_error", ctypes.c_double),
                 ("col_bytes", ctypes.c_double), ("col_flops", ctypes.c_double),
-                ("phase_ms", ctypes.c_double * 8), ("phase_launches", ctypes.c_int64 * 8)]
+                ("phase_ms", ctypes.c_double * 8), ("phase_launches", ctypes.c_int64 * 8),
+                ("kernel_launches", ctypes.c_int64)]
 
 PHASES = ("propose", "H", "reject", "prep", "colstep", "round_end", "plain_gemv", "plain_finish")
 

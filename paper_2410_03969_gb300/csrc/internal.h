@@ -62,11 +62,14 @@ struct DevBuffers {
   float* Bs32;       // mixed mode: T_max x ldBs rows of the column-step operand
   long long ldBs;
   double* Hpk;       // packed-triangle fallback storage for Algorithm 1
+  double* Hpart;     // kHTilesMax x kHSplitMax x 256 partial products of H
+  int* hcnt;         // kHTilesMax arrival counters (zero between launches)
   double* red;       // reduction scratch (trace error)
   long long nred;
   DevState* st;
   int Tmax;
   int mixed;         // 1: F is float
+  int num_sms;
 };
 
 // Thread-local message returned by rpchol_last_error (rpchol.cu).

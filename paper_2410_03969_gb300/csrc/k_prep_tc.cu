@@ -74,42 +74,54 @@ __global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float
 // (j0 + 16) x 16 floats at offset 256 b (b + 1) / 2, row l contiguous.
 // Rows and columns of L beyond s are taken as the identity, so padded
 // columns of G are copies of the (zero) padded columns of R.
+// Grid: blockIdx.x = b, blockIdx.y = a part of the range l < j0 (part 0
+// also writes the diagonal rows).  Each CTA forms D_b^{-1} itself, by rows
+// (row c is final once rows < c are), one step per row for the whole CTA.
 __global__ void __launch_bounds__(256) k_wblk(const DevState* st, const double* __restrict__ L,
                                               int ldL, float* W) {
+  __shared__ double Db[16][17];
+  __shared__ double acc[16][17];
   __shared__ double Dinv[16][17];
-  __shared__ double Lb[16][kTMax];  // rows j0..j0+15 of L, columns < j0
+  __shared__ double rdiag[16];
+  __shared__ double Lb[16][33];  // rows j0..j0+15 of L, columns l0..l1-1
   if (st->done) return;
   const int s = st->s;
-  const int b = blockIdx.x;
+  const int b = blockIdx.x, part = blockIdx.y, nparts = gridDim.y;
   const int j0 = 16 * b;
   if (j0 >= s) return;
-  const int t = threadIdx.x;
-  auto Lat = [&](int r, int c) -> double {  // L with identity padding beyond s
-    if (r >= s || c >= s) return r == c ? 1.0 : 0.0;
-    return c <= r ? L[(long long)r * ldL + c] : 0.0;
+  const int per = (j0 + nparts - 1) / nparts;  // <= 32
+  const int l0 = part * per;
+  const int l1 = l0 + per < j0 ? l0 + per : j0;
+  if (part > 0 && l0 >= l1) return;
+  const int nl = l1 > l0 ? l1 - l0 : 0;
+  const int t = threadIdx.x, r = t >> 4, m = t & 15;
+  auto Lat = [&](int rr, int cc) -> double {  // L with identity padding beyond s
+    if (rr >= s || cc >= s) return rr == cc ? 1.0 : 0.0;
+    return cc <= rr ? L[(long long)rr * ldL + cc] : 0.0;
   };
-  for (int e = t; e < 16 * j0; e += blockDim.x) Lb[e / j0][e % j0] = Lat(j0 + e / j0, e % j0);
-  // D_b^{-1} column m by forward substitution (16 threads)
-  if (t < 16) {
-    const int m = t;
-    for (int r = 0; r < 16; ++r) {
-      double v = (r == m) ? 1.0 : 0.0;
-      for (int c = m; c < r; ++c) v -= Lat(j0 + r, j0 + c) * Dinv[c][m];
-      Dinv[r][m] = r >= m ? v / Lat(j0 + r, j0 + r) : 0.0;
-    }
-  }
+  Db[r][m] = Lat(j0 + r, j0 + m);
+  acc[r][m] = r == m ? 1.0 : 0.0;
+  if (t < 16) rdiag[t] = 1.0 / Lat(j0 + t, j0 + t);
+  for (int e = t; e < 16 * nl; e += 256) Lb[e / nl][e % nl] = Lat(j0 + e / nl, l0 + e % nl);
   __syncthreads();
+  // D_b^{-1}(c, :) = (e_c - sum_{c' < c} D_b(c, c') D_b^{-1}(c', :)) / D_b(c, c)
+  for (int c = 0; c < 16; ++c) {
+    if (r >= c) {
+      const double xc = acc[c][m] * rdiag[c];
+      if (r == c) Dinv[c][m] = xc;
+      else acc[r][m] = fma(-Db[r][c], xc, acc[r][m]);
+    }
+    __syncthreads();
+  }
   float* Wb = W + 256 * (long long)b * (b + 1) / 2;
-  for (int e = t; e < 16 * j0; e += blockDim.x) {  // W_b(l, jj), l < j0
+  for (int e = t; e < 16 * nl; e += 256) {  // W_b(l, jj), l0 <= l < l1
     const int l = e >> 4, jj = e & 15;
-    double acc = 0.0;
-    for (int m = 0; m <= jj; ++m) acc += Dinv[jj][m] * Lb[m][l];
-    Wb[(long long)l * 16 + jj] = (float)(-acc);
+    double a = 0.0;
+    for (int mm = 0; mm <= jj; ++mm) a = fma(Dinv[jj][mm], Lb[mm][l], a);
+    Wb[(long long)(l0 + l) * 16 + jj] = (float)(-a);
   }
-  for (int e = t; e < 256; e += blockDim.x) {  // W_b(j0 + m, jj) = D_b^{-1}(jj, m)
-    const int m = e >> 4, jj = e & 15;
-    Wb[(long long)(j0 + m) * 16 + jj] = (float)Dinv[jj][m];
-  }
+  if (part == 0)  // W_b(j0 + m, jj) = D_b^{-1}(jj, m)
+    Wb[(long long)(j0 + r) * 16 + m] = (float)Dinv[m][r];
 }
 
 __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, float* Xl) {
@@ -124,7 +136,7 @@ __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, f
 cudaError_t launch_prep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
   k_prep_tc<<<kTMax, 256, 0, s>>>(b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc,
                                   m.FShp, m.FSlp, m.XShp, m.XSlp, m.nrmS);
-  k_wblk<<<kTMax / 16, 256, 0, s>>>(b.st, b.L, b.Tmax, m.Linv32);
+  k_wblk<<<dim3(kTMax / 16, 8), 256, 0, s>>>(b.st, b.L, b.Tmax, m.Linv32);
   return cudaGetLastError();
 }
 

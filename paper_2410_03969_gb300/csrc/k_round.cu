@@ -64,107 +64,104 @@ __device__ __forceinline__ double warp_incl_scan(double v) {
   return v;
 }
 
-// Step 1 of Algorithm 2: T iid draws with P{j} = d_j / sum(d).  One CTA of
-// 1024 threads.  The tile sums (written by the kernel that last updated d)
-// are scanned into tile_prefix; each draw binary-searches the tile prefix
-// and then scans its tile with a warp prefix sum: the pivot is the first j
-// whose running sum exceeds U * W (the proposal map of the oracle, summed
-// in tile order instead of index order).
-__global__ void __launch_bounds__(1024) k_propose(DevState* st, const double* __restrict__ dvec,
-                                                  const double* __restrict__ tile_sums,
-                                                  double* tile_prefix, long long ntiles,
-                                                  long long N, int* prop, double* uprop,
-                                                  double* uacc, int use_smem) {
+// Step 1 of Algorithm 2: T iid draws with P{j} = d_j / sum(d).  FP64 is
+// scarce on this GPU, so the draws are spread over ceil(T / 8) CTAs, one
+// warp per draw, and every CTA forms the same inclusive prefix of the tile
+// sums (written by the kernel that last updated d): thread t sums its run of
+// consecutive tiles sequentially, then a block scan combines the runs, in a
+// fixed order identical in every CTA.  A draw binary-searches the tile
+// prefix and scans its tile with a warp prefix sum: the pivot is the first j
+// whose running sum exceeds U * W (the proposal map of the oracle, summed in
+// tile order instead of index order).
+__global__ void __launch_bounds__(256) k_propose(DevState* st, const double* __restrict__ dvec,
+                                                 const double* __restrict__ tile_sums,
+                                                 double* tile_prefix, long long ntiles,
+                                                 long long N, int* prop, double* uprop,
+                                                 double* uacc, int use_smem) {
   extern __shared__ double pref_smem[];
-  __shared__ double wsum[32];
-  __shared__ double carry_sh;
+  __shared__ double wsum[8];
   if (st->done) return;
   const int T = st->T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* P = use_smem ? pref_smem : tile_prefix;  // inclusive prefix of the tile sums
-  double run = 0.0;
-  for (long long base = 0; base < ntiles; base += 1024) {
-    const long long t = base + tid;
-    const double v = t < ntiles ? tile_sums[t] : 0.0;
-    double incl = warp_incl_scan(v);
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      double w = wsum[lane];
-      const double wi = warp_incl_scan(w);
-      wsum[lane] = wi - w;  // exclusive prefix of warp totals
-      if (lane == 31) carry_sh = wi;
-    }
-    __syncthreads();
-    incl += wsum[warp];
-    if (t < ntiles) P[t] = run + incl;
-    const double chunk = carry_sh;
-    __syncthreads();
-    run += chunk;
+  double* P = use_smem ? pref_smem : tile_prefix + blockIdx.x * ntiles;
+  const long long per = (ntiles + 255) / 256;
+  const long long t0 = tid * per, t1 = t0 + per < ntiles ? t0 + per : ntiles;
+  double own = 0.0;
+  for (long long t = t0; t < t1; ++t) own += tile_sums[t];
+  double incl = warp_incl_scan(own);
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  double before = 0.0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  double W = 0.0;
+  for (int w = 0; w < 8; ++w) W += wsum[w];
+  double run = before + (incl - own);
+  for (long long t = t0; t < t1; ++t) {
+    run += tile_sums[t];
+    P[t] = run;
   }
-  const double W = run;
-  if (tid == 0) {
+  if (blockIdx.x == 0 && tid == 0) {
     st->W = W;
     if (!(W > 0.0)) st->done = 1;
   }
   if (!(W > 0.0)) return;
   __syncthreads();  // prefix complete and visible to the CTA
 
+  const int j = blockIdx.x * 8 + warp;
+  if (j >= T) return;
   const unsigned long long seed = st->seed;
   const unsigned round = (unsigned)st->round;
   const unsigned inst = st->instance;
-  for (int j = warp; j < T; j += 32) {
-    double up = 0.0, ua = 0.0;
-    if (lane == 0) uniforms(seed, (unsigned)j, round, inst, &up, &ua);
-    up = __shfl_sync(0xffffffffu, up, 0);
-    ua = __shfl_sync(0xffffffffu, ua, 0);
-    const double target = up * W;
-    // first tile whose inclusive prefix exceeds the target
-    long long lo = 0, hi = ntiles;
-    while (lo < hi) {
-      const long long mid = (lo + hi) >> 1;
-      if (P[mid] > target) hi = mid;
-      else lo = mid + 1;
-    }
-    long long t = lo;
-    bool fallback = false;
-    if (t >= ntiles) {  // rounding left no tile: the last tile with weight
-      fallback = true;
-      t = ntiles - 1;
-      while (t > 0 && !(tile_sums[t] > 0.0)) --t;
-    }
-    const long long r0 = t * kTileRows;
-    const long long r1 = r0 + kTileRows < N ? r0 + kTileRows : N;
-    double running = t > 0 ? P[t - 1] : 0.0;
-    long long found = -1, last_pos = -1;
-    for (long long c = r0; c < r1; c += 32) {
-      const long long r = c + lane;
-      const double v = r < r1 ? dvec[r] : 0.0;
-      const double incl = warp_incl_scan(v);
-      const unsigned pos = __ballot_sync(0xffffffffu, v > 0.0);
-      if (pos) last_pos = c + 31 - __clz(pos);
-      if (!fallback) {
-        const unsigned hit = __ballot_sync(0xffffffffu, v > 0.0 && running + incl > target);
-        if (hit) {
-          found = c + __ffs(hit) - 1;
-          break;
-        }
+  double up = 0.0, ua = 0.0;
+  if (lane == 0) uniforms(seed, (unsigned)j, round, inst, &up, &ua);
+  up = __shfl_sync(0xffffffffu, up, 0);
+  ua = __shfl_sync(0xffffffffu, ua, 0);
+  const double target = up * W;
+  // first tile whose inclusive prefix exceeds the target
+  long long lo = 0, hi = ntiles;
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    if (P[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  long long t = lo;
+  bool fallback = false;
+  if (t >= ntiles) {  // rounding left no tile: the last tile with weight
+    fallback = true;
+    t = ntiles - 1;
+    while (t > 0 && !(tile_sums[t] > 0.0)) --t;
+  }
+  const long long r0 = t * kTileRows;
+  const long long r1 = r0 + kTileRows < N ? r0 + kTileRows : N;
+  double running = t > 0 ? P[t - 1] : 0.0;
+  long long found = -1, last_pos = -1;
+  for (long long c = r0; c < r1; c += 32) {
+    const long long r = c + lane;
+    const double v = r < r1 ? dvec[r] : 0.0;
+    const double inc = warp_incl_scan(v);
+    const unsigned pos = __ballot_sync(0xffffffffu, v > 0.0);
+    if (pos) last_pos = c + 31 - __clz(pos);
+    if (!fallback) {
+      const unsigned hit = __ballot_sync(0xffffffffu, v > 0.0 && running + inc > target);
+      if (hit) {
+        found = c + __ffs(hit) - 1;
+        break;
       }
-      running += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (found < 0) found = last_pos;  // rounding: the last positive weight in the tile
-    if (found < 0) found = r0;         // unreachable when W > 0
-    if (lane == 0) {
-      prop[j] = (int)found;
-      uprop[j] = dvec[found];
-      uacc[j] = ua;
-    }
+    running += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (found < 0) found = last_pos;  // rounding: the last positive weight in the tile
+  if (found < 0) found = r0;         // unreachable when W > 0
+  if (lane == 0) {
+    prop[j] = (int)found;
+    uprop[j] = dvec[found];
+    uacc[j] = ua;
   }
 }
 
 cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s) {
-  (void)T;
-  // the tile prefix lives in shared memory up to 20,480 tiles (N <= 2.6M)
+  // the tile prefix lives in shared memory up to 20,480 tiles (N <= 2.6M),
+  // otherwise in a global array with one copy per CTA
   const size_t bytes = (size_t)b.ntiles * sizeof(double);
   const int use_smem = bytes <= 160 * 1024 ? 1 : 0;
   static bool attr = false;
@@ -174,48 +171,92 @@ cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_propose<<<1, 1024, use_smem ? bytes : 0, s>>>(b.st, b.dvec, b.tile_sums, b.tile_prefix,
-                                                  b.ntiles, b.N, b.prop, b.uprop, b.uacc,
-                                                  use_smem);
+  const int grid = (T + 7) / 8;
+  k_propose<<<grid, 256, use_smem ? bytes : 0, s>>>(b.st, b.dvec, b.tile_sums, b.tile_prefix,
+                                                    b.ntiles, b.N, b.prop, b.uprop, b.uacc,
+                                                    use_smem);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ H
 // H = A(S',S') - F(S',:) F(S',:)^*, FP64 (FP32 factors are widened; their
 // products are exact in FP64).  Kernel entries by direct differences.
-// 8 x 8 output tiles, lower-triangle tiles only (H is symmetric; both
-// halves are written from the same value), F rows staged 32 columns at a
-// time.
+// Output tiles of 16 x 16 (lower triangle of tiles; both halves of H are
+// written from the same value), one thread per entry.  FP64 throughput is
+// low on this GPU, so the rank dimension is split KS = gridDim.y ways to
+// spread the tiles over all SMs: each CTA writes a partial product, and the
+// last CTA of a tile to finish (counted with an atomic) adds the KS partials
+// in the fixed order z = 0..KS-1, so the result does not depend on timing.
 template <typename TF>
-__global__ void __launch_bounds__(64) k_hmat(const DevState* st, const float* __restrict__ X,
-                                             int xld, int d, int kind, double inv_sigma,
-                                             const TF* __restrict__ F, long long ldF,
-                                             const int* __restrict__ prop, double* H) {
-  __shared__ double Fa[8][33];
-  __shared__ double Fb[8][33];
+__global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* __restrict__ X,
+                                              int xld, int d, int kind, double inv_sigma,
+                                              const TF* __restrict__ F, long long ldF,
+                                              const int* __restrict__ prop, double* H,
+                                              double* Hpart, int* hcnt) {
+  __shared__ double Fa[16][33];
+  __shared__ double Fb[16][33];
+  __shared__ int last;
   if (st->done) return;
-  if (blockIdx.x > blockIdx.y) return;
   const int T = st->T;
   const long long rank = st->rank;
-  const int a0 = blockIdx.y * 8, b0 = blockIdx.x * 8;
+  const int KS = gridDim.y, z = blockIdx.y;
+  const int tile = blockIdx.x;  // lower tile (ta, tb), tb <= ta, row-major
+  int ta = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+  while ((ta + 1) * (ta + 2) / 2 <= tile) ++ta;
+  while (ta * (ta + 1) / 2 > tile) --ta;
+  const int tb = tile - ta * (ta + 1) / 2;
+  const int a0 = 16 * ta, b0 = 16 * tb;
   if (a0 >= T) return;
-  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
-  double acc = 0.0;
-  for (long long m0 = 0; m0 < rank; m0 += 32) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long long kc = ((rank + KS - 1) / KS + 31) & ~31ll;
+  const long long m_lo = z * kc;
+  const long long m_hi = m_lo + kc < rank ? m_lo + kc : rank;
+  // rows of this thread's two staged elements (row e >> 5, column e & 31)
+  int ra[2], rb[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 64 * q;  // 0..255: row e >> 5, column e & 31
-      const int r = e >> 5, cc = e & 31;
-      const long long m = m0 + cc;
-      const int ra = a0 + r < T ? prop[a0 + r] : prop[0];
-      const int rb = b0 + r < T ? prop[b0 + r] : prop[0];
-      Fa[r][cc] = m < rank ? (double)F[(long long)ra * ldF + m] : 0.0;
-      Fb[r][cc] = m < rank ? (double)F[(long long)rb * ldF + m] : 0.0;
+  for (int q = 0; q < 2; ++q) {
+    const int r = (tid + 256 * q) >> 5;
+    ra[q] = a0 + r < T ? prop[a0 + r] : prop[0];
+    rb[q] = b0 + r < T ? prop[b0 + r] : prop[0];
+  }
+  const int cc = tid & 31;
+  TF va[2], vb[2];  // the next chunk, loaded while the current one is used
+  auto fetch = [&](long long m0) {
+    const long long m = m0 + cc;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      va[q] = m < m_hi ? F[(long long)ra[q] * ldF + m] : (TF)0;
+      vb[q] = m < m_hi ? F[(long long)rb[q] * ldF + m] : (TF)0;
+    }
+  };
+  double acc = 0.0;
+  if (m_lo < m_hi) fetch(m_lo);
+  for (long long m0 = m_lo; m0 < m_hi; m0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int r = (tid + 256 * q) >> 5;
+      Fa[r][cc] = (double)va[q];
+      Fb[r][cc] = (double)vb[q];
     }
     __syncthreads();
+    if (m0 + 32 < m_hi) fetch(m0 + 32);
 #pragma unroll 8
-    for (int q = 0; q < 32; ++q) acc += Fa[ty][q] * Fb[tx][q];
+    for (int q = 0; q < 32; ++q) acc = fma(Fa[ty][q], Fb[tx][q], acc);
     __syncthreads();
+  }
+  double sum = acc;
+  if (KS > 1) {
+    double* P = Hpart + (long long)tile * KS * 256;
+    P[z * 256 + tid] = acc;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&hcnt[tile], 1) == KS - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    sum = 0.0;
+    for (int zz = 0; zz < KS; ++zz) sum += __ldcg(P + zz * 256 + tid);
+    if (tid == 0) hcnt[tile] = 0;
   }
   const int a = a0 + ty, bcol = b0 + tx;
   if (a < T && bcol < T && bcol <= a) {
@@ -231,43 +272,94 @@ __global__ void __launch_bounds__(64) k_hmat(const DevState* st, const float* __
       }
       kv = phi_r2<double>(kind, inv_sigma, r2);
     }
-    const double h = kv - acc;
+    const double h = kv - sum;
     H[(long long)a * T + bcol] = h;
     H[(long long)bcol * T + a] = h;
   }
 }
 
 cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s) {
-  const int nb = (T + 7) / 8;
-  dim3 grid(nb, nb);
+  const int nb = (T + 15) / 16;
+  const int ntile = nb * (nb + 1) / 2;
+  int ks = (4 * b.num_sms + ntile - 1) / ntile;
+  if (ks > kHSplitMax) ks = kHSplitMax;
+  if (ks < 1) ks = 1;
+  dim3 grid(ntile, ks);
   if (b.mixed)
-    k_hmat<float><<<grid, 64, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
-                                      (const float*)b.F, b.ldF, b.prop, b.H);
+    k_hmat<float><<<grid, 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
+                                       (const float*)b.F, b.ldF, b.prop, b.H, b.Hpart, b.hcnt);
   else
-    k_hmat<double><<<grid, 64, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
-                                       (const double*)b.F, b.ldF, b.prop, b.H);
+    k_hmat<double><<<grid, 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
+                                        (const double*)b.F, b.ldF, b.prop, b.H, b.Hpart, b.hcnt);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ Algorithm 1
-// RejectionSampleSubmatrix in one CTA.  The lower triangle of H lives packed
-// (row j at offset j(j+1)/2) in shared memory when it fits, otherwise in a
-// global scratch array.  For i = 0..T-1: accept iff u_i * U_i < h_ii with
-// u_i the proposal weight d[s'_i]; on acceptance L(i:T, i) = H(i:T, i) /
-// sqrt(h_ii) and the trailing triangle is downdated.  Stops once the total
-// rank reaches k.  Writes the compact L, the accepted pivots and s.
+// RejectionSampleSubmatrix in one CTA.  For i = 0..T-1: accept iff
+// u_i * U_i < h_ii (u_i the proposal weight d[s'_i], h_ii the current Schur
+// diagonal); on acceptance L(i:T, i) = H(i:T, i) / sqrt(h_ii) and the
+// trailing triangle is downdated.  Stops once the total rank reaches k.
+// Writes the compact L, the accepted pivots and s.
+//
+// FP64 issue is the limit here (one warp retires an FP64 instruction about
+// every 64 cycles, an SM about every 16 to 19), so the right-looking factorisation
+// runs with a lookahead of one pivot.  In the iteration of accepted pivot t
+// (index n_t):
+//   - the lead warps form column t: the downdate of pivot t-1 is applied to
+//     column n_t alone, then scaled by 1 / sqrt(h); they downdate the
+//     diagonal, which they keep apart from H, and warp 0 finds the next
+//     acceptance (from its own 32 rows without waiting for the others,
+//     unless none of them accepts) and its reciprocal square root;
+//   - at the same time nine other warps apply the downdate of pivot t-1 to
+//     the rows and columns beyond n_t (the only entries later pivots read),
+//     folded so that every warp instruction has all lanes busy; none of
+//     them issues on warp 0's sub-partition, so the FP64 pipe there serves
+//     the lead chain alone.
+// Rejections leave H untouched, so the acceptance test looks at 32
+// proposals at once.  The lower triangle of H lives packed (row j at offset
+// j(j+1)/2) in shared memory when it fits, otherwise in a global scratch.
 __device__ __forceinline__ long long pk(int j, int l) { return (long long)j * (j + 1) / 2 + l; }
 
-__global__ void __launch_bounds__(512) k_reject(DevState* st, const double* __restrict__ H,
-                                                const double* __restrict__ uprop,
-                                                const double* __restrict__ uacc,
-                                                const int* __restrict__ prop, double* Lw,
-                                                double* L, int ldL, int* Sacc, long long* piv,
-                                                double* Hglobal, int use_smem) {
+// x^{-1/2} by Newton-Raphson on f(y) = y^{-2} - x, y <- y (3 - x y^2) / 2,
+// started from the single-precision hardware estimate: each step squares
+// the relative error, so two steps take its 2^-23 below FP64 rounding.  The
+// narrowing to float and the widening back are done on the bit patterns
+// (exponent rebased by 1023 - 127, mantissa truncated), which is exact
+// enough for a seed and keeps the conversions off the FP64 pipe.
+// Arguments outside [1e-30, 1e30] take sqrt and divide.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  const long long xb = __double_as_longlong(x);
+  const float xf = __int_as_float((int)((xb >> 29) - (896ll << 23)));
+  const float rf = rsqrtf(xf);
+  double y = __longlong_as_double(((long long)__float_as_int(rf) + (896ll << 23)) << 29);
+  const double hx = 0.5 * x;
+  y = y * fma(-hx * y, y, 1.5);
+  y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+
+// u < h for u >= +0 as an integer comparison of the bit patterns (FP64
+// comparisons issue at the FP64 rate); NaN h rejects, like the FP compare.
+__device__ __forceinline__ bool accept_bits(long long ub, double h) {
+  const long long hb = __double_as_longlong(h);
+  return hb <= 0x7ff0000000000000ll && ub < hb;
+}
+
+constexpr int kRejectThreads = 512;
+constexpr int kLeadWarps = 4;
+
+__global__ void __launch_bounds__(kRejectThreads) k_reject(
+    DevState* st, const double* __restrict__ H, const double* __restrict__ uprop,
+    const double* __restrict__ uacc, const int* __restrict__ prop, double* Lw, double* L, int ldL,
+    int* Sacc, long long* piv, double* Hglobal, int use_smem) {
   extern __shared__ double dyn[];
-  __shared__ double lc[kTMax];
-  __shared__ double us[kTMax];
+  __shared__ double lcb[2][kTMax];  // column of accepted pivot t in lcb[t & 1]
+  __shared__ double dg[kTMax];      // current Schur diagonal
+  __shared__ long long ub[kTMax];   // u_i U_i, bit pattern of a non-negative double
   __shared__ int accl[kTMax];
+  __shared__ int nxt_sh[2];
+  __shared__ double inv_sh[2];
   if (st->done) return;
   const int T = st->T;
   const long long rank = st->rank;
@@ -278,30 +370,109 @@ __global__ void __launch_bounds__(512) k_reject(DevState* st, const double* __re
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int j = warp; j < T; j += nw)
     for (int l = lane; l <= j; l += 32) Hp[pk(j, l)] = H[(long long)j * T + l];
-  for (int i = tid; i < T; i += nt) us[i] = uprop[i] * uacc[i];
+  for (int i = tid; i < T; i += nt) {
+    dg[i] = H[(long long)i * T + i];
+    const long long u = __double_as_longlong(uprop[i] * uacc[i]);
+    ub[i] = u < 0 ? 0 : u;  // -0 -> +0
+    lcb[1][i] = 0.0;        // "column -1": no downdate before pivot 0
+  }
   __syncthreads();
-  int n = 0;
-  for (int i = 0; i < T; ++i) {
-    if (n >= maxacc) break;
-    const double h = Hp[pk(i, i)];
-    if (us[i] < h) {
-      const double inv = 1.0 / sqrt(h);
-      for (int j = i + tid; j < T; j += nt) {
-        const double v = Hp[pk(j, i)] * inv;
-        lc[j] = v;
-        Lw[(long long)j * kTMax + n] = v;
-      }
-      if (tid == 0) accl[n] = i;
-      __syncthreads();
-      for (int j = i + 1 + warp; j < T; j += nw) {
-        const double lj = lc[j];
-        for (int l = i + 1 + lane; l <= j; l += 32) Hp[pk(j, l)] -= lj * lc[l];
-      }
-      ++n;
-      __syncthreads();
+
+  // first acceptance at or after i0 (warp 0), T if none
+  auto next_accept = [&](int i0) -> int {
+    for (int c = i0; c < T; c += 32) {
+      const int i = c + lane;
+      const unsigned m = __ballot_sync(0xffffffffu, i < T && accept_bits(ub[i], dg[i]));
+      if (m) return c + __ffs(m) - 1;
+    }
+    return T;
+  };
+  if (warp == 0) {
+    const int nx = maxacc > 0 ? next_accept(0) : T;
+    if (lane == 0) {
+      nxt_sh[0] = nx;
+      inv_sh[0] = nx < T ? rsqrt_newton(dg[nx]) : 0.0;
     }
   }
   __syncthreads();
+
+  int t = 0;
+  for (;; ++t) {
+    const int n_t = nxt_sh[t & 1];
+    if (n_t >= T) break;
+    const double* lp = lcb[(t + 1) & 1];  // column of pivot t - 1
+    if (warp < kLeadWarps) {
+      const double inv = inv_sh[t & 1];
+      const double lpn = lp[n_t];
+      double* lc = lcb[t & 1];
+      // column t below the pivot; warp 0 owns rows n_t+1..n_t+32, the ones
+      // the next acceptance test looks at first
+      double dwin = 0.0;
+      for (int j = n_t + 1 + tid; j < T; j += 32 * kLeadWarps) {
+        const double v = fma(-lp[j], lpn, Hp[pk(j, n_t)]) * inv;
+        lc[j] = v;
+        Lw[(long long)j * kTMax + t] = v;
+        const double dn = fma(-v, v, dg[j]);
+        dg[j] = dn;
+        if (j < n_t + 1 + 32 * kLeadWarps) dwin = dn;
+      }
+      if (tid == 32 * kLeadWarps - 1) {  // the pivot's own entry, h / sqrt(h)
+        const double v = fma(-lpn, lpn, Hp[pk(n_t, n_t)]) * inv;
+        lc[n_t] = v;
+        Lw[(long long)n_t * kTMax + t] = v;
+      }
+      if (warp == 0) {
+        // the next acceptance from warp 0's own rows when there is one there,
+        // without waiting for the other lead warps
+        int nx = T;
+        bool waited = false;
+        double hx = 0.0;
+        if (t + 1 < maxacc) {
+          const int i = n_t + 1 + lane;
+          const unsigned m = __ballot_sync(0xffffffffu, i < T && accept_bits(ub[i], dwin));
+          if (m) {
+            const int src = __ffs(m) - 1;
+            nx = n_t + 1 + src;
+            hx = __shfl_sync(0xffffffffu, dwin, src);
+          } else {
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+            waited = true;
+            nx = next_accept(n_t + 33);
+            if (nx < T) hx = dg[nx];
+          }
+        }
+        if (lane == 0) {
+          nxt_sh[(t + 1) & 1] = nx;
+          inv_sh[(t + 1) & 1] = nx < T ? rsqrt_newton(hx) : 0.0;
+          accl[t] = n_t;
+        }
+        if (!waited) asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+      } else {
+        asm volatile("bar.arrive 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+      }
+    } else if (t > 0 && (warp & 3) != 0) {
+      // downdate of pivot t - 1 on rows and columns base..T-1: row base + r
+      // is paired with row base + m - 1 - r, m + 1 entries together.  Warps
+      // 4, 8, 12 stay idle: they share warp 0's scheduler (warp w issues on
+      // sub-partition w mod 4), whose FP64 pipe is kept for the lead chain.
+      const int base = n_t + 1, m = T - base;
+      const int tw = (warp >> 2) * 3 + (warp & 3) - 4;
+      const int ntw = (nw >> 2) * 3 - 3;
+      for (int r = tw; r < (m + 1) / 2; r += ntw) {
+        const int ra = base + r, rb = base + m - 1 - r;
+        const int lenA = r + 1;
+        const int tot = ra == rb ? lenA : m + 1;
+        for (int q = lane; q < tot; q += 32) {
+          const int j = q < lenA ? ra : rb;
+          const int l = base + (q < lenA ? q : q - lenA);
+          const long long o = pk(j, l);
+          Hp[o] = fma(-lp[j], lp[l], Hp[o]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int n = t;
   for (int e = tid; e < n * n; e += nt) {
     const int a = e / n, c = e % n;
     L[(long long)a * ldL + c] = c <= a ? Lw[(long long)accl[a] * kTMax + c] : 0.0;
@@ -319,7 +490,8 @@ __global__ void __launch_bounds__(512) k_reject(DevState* st, const double* __re
 
 cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s) {
   const size_t packed = (size_t)T * (T + 1) / 2 * sizeof(double);
-  const size_t static_bytes = sizeof(double) * 2 * kTMax + sizeof(int) * kTMax;
+  const size_t static_bytes = sizeof(double) * 4 * kTMax + sizeof(long long) * kTMax +
+                              sizeof(int) * kTMax + 64;
   const size_t limit = 227 * 1024 - static_bytes - 1024;
   const int use_smem = packed <= limit ? 1 : 0;
   const size_t dyn = use_smem ? packed : 0;
@@ -328,8 +500,8 @@ cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s) {
                                          (int)dyn);
     if (e != cudaSuccess) return e;
   }
-  k_reject<<<1, 512, dyn, s>>>(b.st, b.H, b.uprop, b.uacc, b.prop, b.Lw, b.L, b.Tmax, b.Sacc,
-                               b.piv, b.Hpk, use_smem);
+  k_reject<<<1, kRejectThreads, dyn, s>>>(b.st, b.H, b.uprop, b.uacc, b.prop, b.Lw, b.L, b.Tmax,
+                                          b.Sacc, b.piv, b.Hpk, use_smem);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ struct rpchol_ctx {
   DevState* st_host = nullptr;             // pinned mirror
   int last_plain = 0;
   int has_run = 0;
+  long long host_iters = -1;  // loop bodies the host loop launched (-1: graph)
   int profile = 0;
   std::vector<ProfRec> prof;  // events of the last profiled run
   int use_tc = 0;             // mixed mode: tensor-core column step
@@ -289,6 +290,7 @@ rpchol_status run_common(rpchol_ctx* c, int plain, long long k, int T, unsigned 
   CU(launch_reset(c->b, k, T, seed, c->instance, plain, max_rounds, c->stream));
   c->last_plain = plain;
   c->has_run = 1;
+  c->host_iters = -1;
   if (c->use_graph && !c->profile) {
     cudaGraphExec_t ex;
     rpchol_status st = get_graph(c, plain, T, &ex);
@@ -303,6 +305,7 @@ rpchol_status run_common(rpchol_ctx* c, int plain, long long k, int T, unsigned 
       cudaError_t e = launch_body(c, plain, T, 0ull, 0, c->stream,
                                   c->profile ? &c->prof : nullptr, it);
       if (e != cudaSuccess) return cuda_fail(e, "round launch");
+      c->host_iters = it + 1;
     }
     CU(cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -394,6 +397,14 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   b.ldB = b.ldF + kTMax;
   b.ldBs = 0;
   b.nred = 2 + 2048 + 2;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm < 1)
+      nsm = 148;
+    b.num_sms = nsm;
+  }
 
   rpchol_status rs = RPCHOL_OK;
   auto fail = [&](rpchol_status s) {
@@ -426,7 +437,9 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   }
   ALLOC(dvec, double, N);
   ALLOC(tile_sums, double, b.ntiles);
-  ALLOC(tile_prefix, double, b.ntiles);
+  // one prefix copy per sampler CTA when the prefix does not fit in shared memory
+  ALLOC(tile_prefix, double,
+        b.ntiles * sizeof(double) <= 160 * 1024 ? b.ntiles : b.ntiles * (kTMax / 8));
   if ((rs = dev_alloc(c, &p, fbytes)) != RPCHOL_OK) return fail(rs);
   b.F = p;
   ALLOC(piv, long long, k_max);
@@ -439,6 +452,8 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   ALLOC(Linv, double, (size_t)kTMax * T_max);
   ALLOC(Sacc, int, kTMax);
   ALLOC(Hpk, double, (size_t)kTMax * (kTMax + 1) / 2);
+  ALLOC(Hpart, double, (size_t)kHTilesMax * kHSplitMax * 256);
+  ALLOC(hcnt, int, kHTilesMax);
   ALLOC(red, double, b.nred);
   ALLOC(st, DevState, 1);
   ALLOC(Bext, double, (size_t)T_max * b.ldB);  // float rows in mixed mode
@@ -448,6 +463,8 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(F)"));
   e = cudaMemsetAsync((void*)b.X, 0, sizeof(float) * (size_t)N * b.xld, c->stream);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(X)"));
+  e = cudaMemsetAsync(b.hcnt, 0, sizeof(int) * kHTilesMax, c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(hcnt)"));
   e = cudaMemsetAsync(b.st, 0, sizeof(DevState), c->stream);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(state)"));
   e = cudaMemsetAsync(b.piv, 0xff, sizeof(long long) * (size_t)k_max, c->stream);
@@ -499,14 +516,7 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
     if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax)) != RPCHOL_OK) return fail(rs);
     m.invd = (float*)q;
     m.err = (int*)((char*)b.st + offsetof(DevState, status));
-    {
-      int dev = 0, nsm = 0;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          nsm < 1)
-        nsm = 148;
-      m.num_sms = nsm;
-    }
+    m.num_sms = b.num_sms;
     e = cudaMemsetAsync(m.FShp, 0, fsbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.FSlp, 0, fsbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.XShp, 0, xsbytes, c->stream);
@@ -648,6 +658,15 @@ rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
   out->trace_error = host[0] / (double)c->b.N;  // tr A = N (phi(0) = 1)
   out->col_bytes = st.col_bytes;
   out->col_flops = st.col_flops;
+  {
+    // kernels of one loop body: accelerated = propose, H, Algorithm 1, operand
+    // prep (two kernels for the tensor-core step), column step, round end;
+    // simple = propose, GEMV, finish, step end.  The graph runs the body once
+    // per round; the host loop launches whole chunks of bodies.
+    const long long per = c->last_plain ? 4 : (c->use_tc ? 7 : 6);
+    const long long iters = c->host_iters >= 0 ? c->host_iters : st.round;
+    out->kernel_launches = c->has_run ? 1 + per * iters : 0;
+  }
   // profile mode: only iterations that did work (those before the final
   // round count; later ones exit at their first instruction) are counted
   for (const auto& r : c->prof) {
