@@ -22,17 +22,21 @@
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
 //   warps 2-3   split each fp32 F tile into TF32 head (in place) and tail
-//   warps 4-11  epilogue, two warps per TMEM lane quarter: the two threads of
-//               a tile row (= TMEM lane) split its columns
-// Operands stream through a two-stage shared-memory ring: per stage a
-// 128 x 32 A tile (head, tail) and an s_pad x 32 B tile (head, tail),
-// 128-byte swizzled, K-major.  The epilogue first drains both accumulators
-// into an R tile in shared memory and releases TMEM, so the next tile's
-// mainloop runs while this tile's substitution and write-out proceed
-// (s_pad <= 128; for larger s the R tile reuses the stage buffers and the
-// producer waits for the epilogue).  Every wait is bounded: on expiry the
-// CTA raises the timeout bit of the run status, drains its own copies and
-// frees its TMEM.
+//   warps 4-7   epilogue group 0, warps 8-11 epilogue group 1: the groups
+//               take alternate tiles; in a group, warp 4 + q (8 + q) owns
+//               TMEM lane quarter q, one thread per tile row.
+// Operands stream through a ring of 2 to 4 shared-memory stages (as many as
+// fit): per stage a 128 x 32 A tile (head, tail) and an s_pad x 32 B tile
+// (head, tail), 128-byte swizzled, K-major.  For s_pad <= 128 the two
+// accumulators of a tile take 256 TMEM columns, so TMEM holds two tiles:
+// the MMAs of the next tile run while an epilogue group works on the last
+// one straight from TMEM (no staging tile in shared memory).  The epilogue
+// evaluates R = kappa - D2 block by block (16 columns), forms G_b with the
+// W blocks, stores G_b back into TMEM over the consumed D1 block (later
+// blocks read it from there) and writes it to F.  For s_pad > 128 one tile
+// holds all of TMEM and tiles alternate with their epilogues.  Every wait is
+// bounded: on expiry the CTA raises the timeout bit of the run status,
+// drains its own copies and frees its TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -46,34 +50,85 @@ constexpr int kTcThreads = 384;
 constexpr int kBM = 128;
 constexpr int kStageA = kBM * 32 * 4;  // 16 KiB
 constexpr int kSmemMax = 227 * 1024;
-constexpr int kSmallBytes = 4 * 1024;  // Sacc, nrmS copies, per-row scratch, barriers
+constexpr int kSmallBytes = 4 * 1024;  // pivots, their norms, barriers, flags, sums
+constexpr int kMaxStages = 4;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct Layout {
-  int s_pad, nbox, stage_bytes, overlap;
-  int rt_off, lt_off, small_off, total;
+  int s_pad, nbox, stage_bytes, stages, nbuf, w_resident, w_off, small_off, total;
 };
 
+// Stages first, then (if room is left for at least as many stages as
+// without it, or three) the whole W of the round, then the small region.
 __host__ __device__ inline Layout make_layout(int s) {
   Layout L;
   L.s_pad = (s + 15) & ~15;
   L.nbox = (L.s_pad + 63) >> 6;
   L.stage_bytes = 2 * kStageA + 2 * L.nbox * 8192;
-  const int stages = 2 * L.stage_bytes;
-  const int rt = kBM * (L.s_pad + 1) * 4;
-  const int lt = 2 * 16 * 1024;  // W blocks: two 16 KiB buffers (or all of W when it fits)
-  L.overlap = (stages + rt + lt + kSmallBytes + 1024) <= kSmemMax ? 1 : 0;
-  if (L.overlap) {
-    L.rt_off = stages;
-    L.lt_off = stages + rt;
-    L.small_off = L.lt_off + lt;
-  } else {
-    L.rt_off = 0;
-    L.lt_off = kBM * 260 * 4;  // after the largest R tile
-    L.small_off = 2 * (2 * kStageA + 2 * 4 * 8192);
-  }
+  L.nbuf = L.s_pad <= 128 ? 2 : 1;
+  const int nblk = L.s_pad >> 4;
+  const int wbytes = 512 * nblk * (nblk + 1);
+  const int budget = kSmemMax - kSmallBytes - 1024;
+  int st_nw = budget / L.stage_bytes;
+  if (st_nw > kMaxStages) st_nw = kMaxStages;
+  int st_w = (budget - wbytes) / L.stage_bytes;
+  if (st_w > kMaxStages) st_w = kMaxStages;
+  const int want = st_nw < 3 ? st_nw : 3;
+  L.w_resident = st_w >= want ? 1 : 0;
+  L.stages = L.w_resident ? st_w : st_nw;
+  L.w_off = L.stages * L.stage_bytes;
+  L.small_off = L.w_off + (L.w_resident ? wbytes : 0);
   L.total = L.small_off + kSmallBytes + 1024;
   return L;
+}
+
+// 16 consecutive floats of a row of F, at a position whose alignment class
+// (column index mod 4) is MIS: scalar stores up to the first 16-byte
+// boundary, then float4 stores.
+template <int MIS>
+__device__ __forceinline__ void store16_al(float* dst, const float* v) {
+  constexpr int c0 = (4 - MIS) & 3;
+  constexpr int c1 = c0 + ((16 - c0) & ~3);
+#pragma unroll
+  for (int j = 0; j < c0; ++j) dst[j] = v[j];
+#pragma unroll
+  for (int j = c0; j < c1; j += 4)
+    *(float4*)(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+#pragma unroll
+  for (int j = c1; j < 16; ++j) dst[j] = v[j];
+}
+
+__device__ __forceinline__ void store16(float* dst, const float* v, int ncols, int mis) {
+  if (ncols >= 16) {
+    switch (mis) {
+      case 0: store16_al<0>(dst, v); break;
+      case 1: store16_al<1>(dst, v); break;
+      case 2: store16_al<2>(dst, v); break;
+      default: store16_al<3>(dst, v); break;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (j < ncols) dst[j] = v[j];
+  }
+}
+
+// acc[jj] += sum_m x[m] W(l0 + m, jj), W rows of 16 floats
+template <int M>
+__device__ __forceinline__ void fma_rows(float* acc, const float* x, const float* W) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float xv = x[m];
+    const float4* wr = (const float4*)(W + 16 * m);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const float4 w = wr[g];
+      acc[4 * g] = fmaf(xv, w.x, acc[4 * g]);
+      acc[4 * g + 1] = fmaf(xv, w.y, acc[4 * g + 1]);
+      acc[4 * g + 2] = fmaf(xv, w.z, acc[4 * g + 2]);
+      acc[4 * g + 3] = fmaf(xv, w.w, acc[4 * g + 3]);
+    }
+  }
 }
 }  // namespace
 
@@ -112,7 +167,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (s == 0) return;
   const long long rank = st->rank;
   const Layout Lo = make_layout(s);
-  const int s_pad = Lo.s_pad, nbox = Lo.nbox, SB = Lo.stage_bytes;
+  const int s_pad = Lo.s_pad, nbox = Lo.nbox, SB = Lo.stage_bytes, NS = Lo.stages;
+  const int nbuf = Lo.nbuf;
   const int nX = a.xld >> 5;
   const int nF = (int)((rank + 31) >> 5);
   const int nch = nX + nF;
@@ -120,41 +176,39 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   unsigned char* small = sm + Lo.small_off;
-  int* Ss = (int*)small;                  // [256] pivots of the round
+  int* Ss = (int*)small;                  // [256] pivots of the round (-1 beyond s)
   float* nrmSs = (float*)(small + 1024);  // [256] their squared norms
-  int* jps = (int*)(small + 2048);        // [128] pivot index found by the second half
-  float* rss = (float*)(small + 2560);    // [128] second half's sum of squares
-  float* rcs = (float*)(small + 3072);    // [128] and its compensation
-  uint64_t* full = (uint64_t*)(small + 3584);  // [2]
-  uint64_t* conv = full + 2;                   // [2]
-  uint64_t* empty = full + 4;                  // [2]
-  uint64_t* accf = full + 6;                   // accumulators of a tile complete
-  uint64_t* tfree = full + 7;                  // epilogue drained TMEM
-  uint64_t* edone = full + 8;                  // epilogue done with shared memory
-  uint32_t* tptr = (uint32_t*)(small + 3584 + 80);
-  volatile int* abort_flag = (volatile int*)(small + 3584 + 84);
-  volatile int* go_flag = (volatile int*)(small + 3584 + 88);
-  double* red = (double*)(small + 3584 + 96);  // [4]
-  float* Rt = (float*)(sm + Lo.rt_off);
-  float* Wsm = (float*)(sm + Lo.lt_off);  // W of the round, whole or two 16 KiB blocks
-  const int nblk_all = (s + 15) >> 4;
-  // resident only when it has its own region (overlap layout) and fits 32 KiB
-  const bool w_resident = Lo.overlap && 128 * nblk_all * (nblk_all + 1) <= 8192;
-  const int ldR = s_pad + 1;
+  uint64_t* full = (uint64_t*)(small + 2048);  // [kMaxStages]
+  uint64_t* conv = full + kMaxStages;          // [kMaxStages]
+  uint64_t* empty = conv + kMaxStages;         // [kMaxStages]
+  uint64_t* accf = empty + kMaxStages;         // [2] accumulators of a tile complete
+  uint64_t* tfree = accf + 2;                  // [2] epilogue done with a TMEM buffer
+  uint32_t* tptr = (uint32_t*)(tfree + 2);
+  volatile int* abort_flag = (volatile int*)(tptr + 1);
+  volatile int* go_flag = abort_flag + 1;      // [2], one per epilogue group
+  double* red = (double*)(small + 2048 + 512);  // [2][4]
+  const float* Wsm = (const float*)(sm + Lo.w_off);
 
   for (int i = threadIdx.x; i < s_pad; i += kTcThreads) {
     Ss[i] = i < s ? a.Sacc[i] : -1;
     nrmSs[i] = i < s ? a.nrmS[i] : 0.f;
   }
+  if (Lo.w_resident) {
+    const int n16 = 32 * (s_pad >> 4) * ((s_pad >> 4) + 1);  // 16-byte pieces of W
+    for (int i = threadIdx.x; i < n16; i += kTcThreads)
+      tc::cp_async16((float*)Wsm + 4 * i, a.W + 4 * i);
+    tc::cp_async_commit();
+  }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&conv[i], 2);   // one arrival per converter warp
       tc::mbar_init(&empty[i], 1);
     }
-    tc::mbar_init(accf, 1);
-    tc::mbar_init(tfree, 8);        // one arrival per epilogue warp
-    tc::mbar_init(edone, 8);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&accf[i], 1);
+      tc::mbar_init(&tfree[i], 4);  // one arrival per warp of an epilogue group
+    }
     *abort_flag = 0;
     tc::fence_mbarrier_init();
   }
@@ -162,6 +216,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::tmem_alloc(tptr, 512);
     tc::tmem_relinquish();
   }
+  tc::cp_async_wait<0>();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tbase = *tptr;
@@ -172,17 +227,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::prefetch_tmap(&tmF);
       const uint32_t bbytes = (uint32_t)nbox * 8192u;
       long long g = 0;  // chunks issued so far (all tiles)
-      int it = 0;
-      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
-        if (!Lo.overlap && it > 0 &&
-            !tc::mbar_wait_bounded(edone, (it - 1) & 1, tc::globaltimer_ns() + kWaitNs,
-                                   abort_flag))
-          break;
+      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         const int row0 = (int)(tile * kBM);
         for (int c = 0; c < nch; ++c, ++g) {
-          const int stg = (int)(g & 1);
-          if (g >= 2 && !tc::mbar_wait_bounded(&empty[stg], (uint32_t)(((g >> 1) - 1) & 1),
-                                               tc::globaltimer_ns() + kWaitNs, abort_flag))
+          const int stg = (int)(g % NS);
+          if (g >= NS && !tc::mbar_wait_bounded(&empty[stg], (uint32_t)(((g / NS) - 1) & 1),
+                                                tc::globaltimer_ns() + kWaitNs, abort_flag))
             break;
           unsigned char* sA = sm + stg * SB;
           unsigned char* sAlo = sA + kStageA;
@@ -209,29 +259,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       if (*abort_flag) {
-        // drain: the (at most two) issued loads not yet consumed must land
+        // drain: the (at most NS) issued loads not yet consumed must land
         volatile int dummy = 0;
         const unsigned long long d2 = tc::globaltimer_ns() + kWaitNs;
-        for (long long q = (g > 2 ? g - 2 : 0); q < g; ++q)
-          tc::mbar_wait_bounded(&full[q & 1], (uint32_t)((q >> 1) & 1), d2, &dummy);
+        for (long long q = (g > NS ? g - NS : 0); q < g; ++q)
+          tc::mbar_wait_bounded(&full[q % NS], (uint32_t)((q / NS) & 1), d2, &dummy);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)s_pad);
-      const uint32_t d1 = tbase;        // columns [0, 256)
-      const uint32_t d2 = tbase + 256;  // columns [256, 512)
       long long g = 0;
       int it = 0;
       for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
-        if (it > 0 && !tc::mbar_wait_bounded(tfree, (it - 1) & 1, tc::globaltimer_ns() + kWaitNs,
-                                             abort_flag))
+        const int buf = it % nbuf;
+        if (it >= nbuf &&
+            !tc::mbar_wait_bounded(&tfree[buf], (uint32_t)(((it / nbuf) - 1) & 1),
+                                   tc::globaltimer_ns() + kWaitNs, abort_flag))
           break;
         tc::tc_fence_after();
+        const uint32_t d1 = tbase + (uint32_t)(buf * 256);           // D1 of this tile
+        const uint32_t d2 = d1 + (nbuf == 2 ? 128u : 256u);           // D2 of this tile
         for (int c = 0; c < nch; ++c, ++g) {
-          const int stg = (int)(g & 1);
-          if (!tc::mbar_wait_bounded(&conv[stg], (uint32_t)((g >> 1) & 1),
+          const int stg = (int)(g % NS);
+          if (!tc::mbar_wait_bounded(&conv[stg], (uint32_t)((g / NS) & 1),
                                      tc::globaltimer_ns() + kWaitNs, abort_flag))
             break;
           tc::tc_fence_after();
@@ -253,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           tc::mma_commit(&empty[stg]);
         }
-        tc::mma_commit(accf);
+        tc::mma_commit(&accf[it & 1]);
       }
     }
   } else if (warp < 4) {
@@ -262,8 +314,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     long long g = 0;
     for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
       for (int c = 0; c < nch; ++c, ++g) {
-        const int stg = (int)(g & 1);
-        if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g >> 1) & 1),
+        const int stg = (int)(g % NS);
+        if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g / NS) & 1),
                                 tc::globaltimer_ns() + kWaitNs, abort_flag))
           break;
         if (c >= nX) {
@@ -290,170 +342,116 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // ------------------------------------------------ epilogue: 8 warps, two per
-    // TMEM lane quarter; the two threads of a row split its columns
-    const int q = warp & 3;            // TMEM lane quarter of this warp
-    const int half = (warp - 4) >> 2;  // 0 for warps 4-7, 1 for warps 8-11
-    const int row = q * 32 + lane;     // tile row = TMEM lane
-    const int et = threadIdx.x - 128;  // 0..255
-    const uint32_t tl = tbase + ((uint32_t)(q * 32) << 16);
-    float* rrow = Rt + row * ldR;
-    // W_b of block b: (16 b + 16) x 16 floats at offset 128 b (b + 1)
-    auto stage_w = [&](int bi, int buf) {
-      const float* src = a.W + 128 * bi * (bi + 1);
-      float* dst = Wsm + buf * 4096;
-      const int n16 = (16 * bi + 16) * 4;  // 16-byte pieces
-      for (int i = et; i < n16; i += 256) tc::cp_async16(dst + 4 * i, src + 4 * i);
-      tc::cp_async_commit();
-    };
-    if (w_resident) {  // all of W fits: stage it once for every tile of this CTA
-      const int n16 = 32 * nblk_all * (nblk_all + 1);
-      for (int i = et; i < n16; i += 256) tc::cp_async16(Wsm + 4 * i, a.W + 4 * i);
-      tc::cp_async_commit();
-      tc::cp_async_wait<0>();
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-    }
-    int it = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    // ------------------------------------------------ epilogue groups
+    const int q = warp & 3;              // TMEM lane quarter of this warp
+    const int grp = (warp - 4) >> 2;     // 0: warps 4-7, 1: warps 8-11
+    const int row = q * 32 + lane;       // tile row = TMEM lane
+    const int gt = row;                  // thread index inside the group
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int nblk = (s + 15) >> 4;
+    const int mis = (int)(rank & 3);
+    const int bar_id = 2 + grp;
+    for (int it = grp;; it += 2) {
+      const long long tile = blockIdx.x + (long long)it * gridDim.x;
+      if (tile >= ntiles) break;
       const long long row0 = tile * kBM;
       const long long grow = row0 + row;
-      tc::mbar_wait_warp(accf, it & 1, tc::globaltimer_ns() + kWaitNs, abort_flag);
-      // one thread's reading of the abort flag decides for all 256
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (et == 0) *go_flag = *abort_flag ? 0 : 1;
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (!*go_flag) {
-        if (et == 0) atomicOr(a.err, (int)kStTimeout);
+      const bool live = grow < a.N;
+      // the row's norm and residual diagonal, and whether it is a pivot row,
+      // while the accumulators fill
+      const float nr = live ? a.nrm[grow] : 0.f;
+      const double dold = live ? a.dvec[grow] : 0.0;
+      int jpiv = -1;
+      for (int j = 0; j < s; ++j)
+        if ((long long)Ss[j] == grow) jpiv = j;
+      tc::mbar_wait_warp(&accf[grp], (uint32_t)((it >> 1) & 1), tc::globaltimer_ns() + kWaitNs,
+                         abort_flag);
+      // one thread's reading of the abort flag decides for the whole group
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (gt == 0) go_flag[grp] = *abort_flag ? 0 : 1;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (!go_flag[grp]) {
+        if (gt == 0) atomicOr(a.err, (int)kStTimeout);
         break;
       }
       tc::tc_fence_after();
-      // ---- drain: R = kappa(D1) - D2 into the R tile (half h: column groups h, h+2, ...)
-      const float nr = grow < a.N ? a.nrm[grow] : 0.f;
-      int jpiv = -1;  // index of this row among the round's pivots, if it is one
-      for (int c0 = 16 * half; c0 < s_pad; c0 += 32) {
-        float v1[16], v2[16], ns[16];
-        int sp[16];
-        // per-column constants into registers first: with the stores to the R
-        // tile below, the compiler could not otherwise reorder these loads
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          sp[j] = Ss[c0 + j];
-          ns[j] = nrmSs[c0 + j];
-        }
-        tc::tmem_ld16_sync(tl + c0, v1);
-        if (nF > 0) {
-          tc::tmem_ld16_sync(tl + 256 + c0, v2);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v2[j] = 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int c = c0 + j;
-          const bool self = (long long)sp[j] == grow;
-          if (self) jpiv = c;
-          const float kv = self ? 1.f : phi_r2<float>(KIND, a.inv_sigma, nr + ns[j] - 2.f * v1[j]);
-          v1[j] = c < s ? kv - v2[j] : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) rrow[c0 + j] = v1[j];
-      }
-      tc::tc_fence_before();
-      tc::mbar_arrive_warp(tfree);  // TMEM may now take the next tile's accumulators
-      if (half == 1) jps[row] = jpiv;
-      asm volatile("bar.sync 1, 256;" ::: "memory");  // R tile complete
-      if (half == 0 && jps[row] >= 0) jpiv = jps[row];
-      // ---- G L^* = R, blocked: G_b = sum_{l < j0 + 16} x_l W_b(l, :) with
-      // x_l = G(:, l) (final) for l < j0 and R(:, l) inside the block; one
-      // small loop per block (the W_b operand is formed in FP64 per round).
-      // Half h computes columns j0 + 8 h .. j0 + 8 h + 7 of the block.
-      float rsq = 0.f, rc = 0.f;  // Kahan-compensated sum of G^2 (this half)
-      const int nblk = (s + 15) >> 4;
-      if (!w_resident) stage_w(0, 0);
+      const uint32_t d1 = tbase + lane_off + (uint32_t)((nbuf == 2 ? grp : 0) * 256);
+      const uint32_t d2 = d1 + (nbuf == 2 ? 128u : 256u);
+      float* frow = a.F + grow * a.ldF + rank;
+      float rsq = 0.f, rc = 0.f;  // Kahan-compensated sum of G^2 over the row
+      // ---- G L^* = R by blocks of 16 columns:
+      //   G_b = sum_{l < j0} G(:, l) W_b(l, :) + sum_m R(:, j0 + m) W_b(j0 + m, :)
       for (int bi = 0; bi < nblk; ++bi) {
         const int j0 = bi * 16;
-        const float* Wb;
-        if (w_resident) {
-          Wb = Wsm + 128 * bi * (bi + 1);
+        const float* Wb = (Lo.w_resident ? Wsm : a.W) + 128 * bi * (bi + 1);
+        float acc[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
+        int lb = 0;
+        for (; lb + 1 < bi; lb += 2) {  // two earlier G blocks per TMEM wait
+          float g0[16], g1[16];
+          tc::tmem_ld16x2_sync(d1 + 16 * lb, d1 + 16 * lb + 16, g0, g1);
+          fma_rows<16>(acc, g0, Wb + 256 * lb);
+          fma_rows<16>(acc, g1, Wb + 256 * (lb + 1));
+        }
+        if (lb < bi) {
+          float g0[16];
+          tc::tmem_ld16_sync(d1 + 16 * lb, g0);
+          fma_rows<16>(acc, g0, Wb + 256 * lb);
+        }
+        // this block of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2
+        float v1[16], v2[16];
+        if (nF > 0) {
+          tc::tmem_ld16x2_sync(d1 + j0, d2 + j0, v1, v2);
         } else {
-          if (bi + 1 < nblk) stage_w(bi + 1, (bi + 1) & 1);
-          else tc::cp_async_commit();
-          tc::cp_async_wait<1>();
-          asm volatile("bar.sync 1, 256;" ::: "memory");
-          Wb = Wsm + (bi & 1) * 4096;
-        }
-        Wb += 8 * half;
-        float acc[8];
+          tc::tmem_ld16_sync(d1 + j0, v1);
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) acc[jj] = 0.f;
-#pragma unroll 4
-        for (int l = 0; l < j0 + 16; ++l) {
-          const float xv = rrow[l];
-          const float4 w0 = *(const float4*)(Wb + l * 16);
-          const float4 w1 = *(const float4*)(Wb + l * 16 + 4);
-          acc[0] = fmaf(xv, w0.x, acc[0]);
-          acc[1] = fmaf(xv, w0.y, acc[1]);
-          acc[2] = fmaf(xv, w0.z, acc[2]);
-          acc[3] = fmaf(xv, w0.w, acc[3]);
-          acc[4] = fmaf(xv, w1.x, acc[4]);
-          acc[5] = fmaf(xv, w1.y, acc[5]);
-          acc[6] = fmaf(xv, w1.z, acc[6]);
-          acc[7] = fmaf(xv, w1.w, acc[7]);
+          for (int m = 0; m < 16; ++m) v2[m] = 0.f;
         }
-        // both halves have read the block's R (and the W buffer) before either
-        // overwrites it
-        asm volatile("bar.sync 1, 256;" ::: "memory");
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) rrow[j0 + 8 * half + jj] = acc[jj];
-        // sum of squares of these 8 values (padded columns are zero), then one
-        // compensated step into the running total
+        for (int m = 0; m < 16; ++m) {
+          const int c = j0 + m;
+          const float kv = c == jpiv ? 1.f
+                                     : phi_r2<float>(KIND, a.inv_sigma, nr + nrmSs[c] - 2.f * v1[m]);
+          v1[m] = c < s ? kv - v2[m] : 0.f;
+        }
+        fma_rows<16>(acc, v1, Wb + 256 * bi);
+        if (jpiv >= 0) {
+          // A pivot row of this round: in exact arithmetic R(S,:) = L L^*, so
+          // G(S_j,:) = L(j,:) and its residual is zero.  The exact values (L
+          // from the FP64 Cholesky of H) replace the rounded contraction, so a
+          // chosen pivot keeps zero proposal weight and its row of F agrees
+          // with the H that later rounds form from it.
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int c = j0 + jj;
+            acc[jj] = (c < s && c <= jpiv) ? (float)a.L[(long long)jpiv * a.ldL + c] : 0.f;
+          }
+        }
+        tc::tmem_st16_sync(d1 + j0, acc);  // G_b over the consumed D1 block
+        if (live) store16(frow + j0, acc, s - j0, mis);
         float bs = 0.f;
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) bs = fmaf(acc[jj], acc[jj], bs);
+        for (int jj = 0; jj < 16; ++jj) bs = fmaf(acc[jj], acc[jj], bs);
         const float y = bs - rc;
         const float t = rsq + y;
         rc = (t - rsq) - y;
         rsq = t;
-        asm volatile("bar.sync 1, 256;" ::: "memory");  // block of G visible to both halves
       }
-      if (half == 1) {
-        rss[row] = rsq;
-        rcs[row] = rc;
+      tc::tc_fence_before();
+      tc::mbar_arrive_warp(&tfree[nbuf == 2 ? grp : 0]);  // TMEM buffer free for tile it + nbuf
+      // ---- residual diagonal (FP64) and the tile's sum of d
+      double dn = 0.0;
+      if (live) {
+        const double v = dold - ((double)rsq - (double)rc);
+        dn = (v > 0.0 && jpiv < 0) ? v : 0.0;
+        a.dvec[grow] = dn;
       }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (half == 0) {
-        // A pivot row of this round: in exact arithmetic R(S,:) = H(S,S) = L L^*,
-        // so G(S_j,:) = L(j,:) and its residual is zero.  Write those exact
-        // values (L from the FP64 Cholesky of H) instead of the rounded
-        // contraction, so that a chosen pivot keeps zero proposal weight and
-        // its row of F agrees with the H that later rounds form from it.
-        if (jpiv >= 0)
-          for (int l = 0; l < s; ++l)
-            rrow[l] = l <= jpiv ? (float)a.L[(long long)jpiv * a.ldL + l] : 0.f;
-        // ---- residual diagonal (FP64) and the tile's sum of d
-        double dn = 0.0;
-        if (grow < a.N) {
-          const double sq = ((double)rsq - (double)rc) + ((double)rss[row] - (double)rcs[row]);
-          const double v = a.dvec[grow] - sq;
-          dn = (v > 0.0 && jpiv < 0) ? v : 0.0;
-          a.dvec[grow] = dn;
-        }
-        double t = dn;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0) red[q] = t;
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (et == 0) a.tile_sums[tile] = red[0] + red[1] + red[2] + red[3];
-      // ---- write G (128 x s) to F(tile, rank : rank + s): rows by warp, columns by lane
-      for (int r = warp - 4; r < kBM; r += 8) {
-        const long long gr = row0 + r;
-        if (gr >= a.N) break;
-        float* dst = a.F + gr * a.ldF + rank;
-        const float* src = Rt + r * ldR;
-        for (int j = lane; j < s; j += 32) dst[j] = src[j];
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");  // R tile and red[] free again
-      if (!Lo.overlap) tc::mbar_arrive_warp(edone);
+      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
+      if (lane == 0) red[grp * 4 + q] = dn;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (gt == 0)
+        a.tile_sums[tile] = red[grp * 4] + red[grp * 4 + 1] + red[grp * 4 + 2] + red[grp * 4 + 3];
     }
   }
   tc::tc_fence_before();
