@@ -61,7 +61,6 @@ struct DevBuffers {
   long long ldB;
   float* Bs32;       // mixed mode: T_max x ldBs rows of the column-step operand
   long long ldBs;
-  double* Hpk;       // packed-triangle fallback storage for Algorithm 1
   double* Hpart;     // kHTilesMax x kHSplitMax x 256 partial products of H
   int* hcnt;         // kHTilesMax arrival counters (zero between launches)
   double* red;       // reduction scratch (trace error)

@@ -295,48 +295,61 @@ cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ Algorithm 1
-// RejectionSampleSubmatrix in one CTA.  For i = 0..T-1: accept iff
-// u_i * U_i < h_ii (u_i the proposal weight d[s'_i], h_ii the current Schur
-// diagonal); on acceptance L(i:T, i) = H(i:T, i) / sqrt(h_ii) and the
-// trailing triangle is downdated.  Stops once the total rank reaches k.
-// Writes the compact L, the accepted pivots and s.
+// RejectionSampleSubmatrix.  For i = 0..T-1: accept iff u_i * U_i < h_ii
+// (u_i the proposal weight d[s'_i], h_ii the current Schur diagonal); on
+// acceptance L(i:T, i) = H(i:T, i) / sqrt(h_ii) and the trailing triangle
+// is downdated.  Stops once the total rank reaches k.  Writes the compact L,
+// the accepted pivots and s.
 //
-// FP64 issue is the limit here (one warp retires an FP64 instruction about
-// every 64 cycles, an SM about every 16 to 19), so the right-looking factorisation
-// runs with a lookahead of one pivot.  In the iteration of accepted pivot t
-// (index n_t):
-//   - the lead warps form column t: the downdate of pivot t-1 is applied to
-//     column n_t alone, then scaled by 1 / sqrt(h); they downdate the
-//     diagonal, which they keep apart from H, and warp 0 finds the next
-//     acceptance (from its own 32 rows without waiting for the others,
-//     unless none of them accepts) and its reciprocal square root;
-//   - at the same time nine other warps apply the downdate of pivot t-1 to
-//     the rows and columns beyond n_t (the only entries later pivots read),
-//     folded so that every warp instruction has all lanes busy; none of
-//     them issues on warp 0's sub-partition, so the FP64 pipe there serves
-//     the lead chain alone.
+// FP64 issue is the limit here: a warp retires an FP64 instruction about
+// every 64 cycles and an SM about every 16 to 19.  The work runs on one
+// thread-block cluster of kRejCluster CTAs with a lookahead of one pivot:
+//   - CTA 0 (the lead CTA) keeps the diagonal apart from H and, in the
+//     iteration of accepted pivot t (index n_t), forms column t: it reads
+//     H(j, n_t) from the CTA that owns row j, applies the downdate of pivot
+//     t-1 to it, scales by 1/sqrt(h), sends the column to every other CTA,
+//     downdates the diagonal, finds the next acceptance (warp 0, from its
+//     own 32 rows unless none of them accepts) and its 1/sqrt(h);
+//   - at the same time CTAs 1.. (row j lives in CTA 1 + j mod (kRejCluster -
+//     1), packed) apply the downdate of pivot t-1 to their rows and columns
+//     beyond n_t, the only entries later pivots read.
+// One cluster barrier separates the iterations.  The lead CTA does no
+// downdate work, so the lead chain has its SM's FP64 pipe to itself.
 // Rejections leave H untouched, so the acceptance test looks at 32
-// proposals at once.  The lower triangle of H lives packed (row j at offset
-// j(j+1)/2) in shared memory when it fits, otherwise in a global scratch.
-__device__ __forceinline__ long long pk(int j, int l) { return (long long)j * (j + 1) / 2 + l; }
+// proposals at once.
+constexpr int kRejCluster = 8;
+constexpr int kRejOwners = kRejCluster - 1;
+constexpr int kRejectThreads = 256;
+constexpr int kLeadWarps = 4;
 
-// x^{-1/2} by Newton-Raphson on f(y) = y^{-2} - x, y <- y (3 - x y^2) / 2,
-// started from the single-precision hardware estimate: each step squares
-// the relative error, so two steps take its 2^-23 below FP64 rounding.  The
-// narrowing to float and the widening back are done on the bit patterns
-// (exponent rebased by 1023 - 127, mantissa truncated), which is exact
-// enough for a seed and keeps the conversions off the FP64 pipe.
-// Arguments outside [1e-30, 1e30] take sqrt and divide.
-__device__ __forceinline__ double rsqrt_newton(double x) {
+// offset of row j in its owner's packed rows: row j = o + kRejOwners i with
+// o = j mod kRejOwners, preceded by rows o + kRejOwners i' (i' < i)
+__device__ __forceinline__ int own_off(int j) {
+  const int o = j % kRejOwners, i = j / kRejOwners;
+  return i * (o + 1) + kRejOwners * i * (i - 1) / 2;
+}
+
+// x^{-1/2} by one Newton-Raphson step on f(y) = y^{-2} - x,
+// y1 = y0 + (y0 / 2)(1 - x y0^2), from the single-precision hardware
+// estimate y0: the step squares its relative error (about 2^-22) to below
+// 1e-13.  The narrowing of x to float and the widening of y0 and y0/2 back
+// are done on the bit patterns (exponent rebased by 1023 - 127; y0 / 2 is
+// exact), so that only the three operations of the step use the FP64 pipe.
+// FP64 mode takes a second step (about 1 ulp).  Arguments outside
+// [1e-30, 1e30] take sqrt and divide.
+__device__ __forceinline__ double rsqrt_newton(double x, bool second) {
   if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
   const long long xb = __double_as_longlong(x);
   const float xf = __int_as_float((int)((xb >> 29) - (896ll << 23)));
   const float rf = rsqrtf(xf);
-  double y = __longlong_as_double(((long long)__float_as_int(rf) + (896ll << 23)) << 29);
-  const double hx = 0.5 * x;
-  y = y * fma(-hx * y, y, 1.5);
-  y = y * fma(-hx * y, y, 1.5);
-  return y;
+  const double y = __longlong_as_double(((long long)__float_as_int(rf) + (896ll << 23)) << 29);
+  const double hy =
+      __longlong_as_double(((long long)__float_as_int(0.5f * rf) + (896ll << 23)) << 29);
+  const double r = fma(-x * y, y, 1.0);
+  const double y1 = fma(hy, r, y);
+  if (!second) return y1;
+  const double r1 = fma(-x * y1, y1, 1.0);
+  return fma(0.5 * y1, r1, y1);
 }
 
 // u < h for u >= +0 as an integer comparison of the bit patterns (FP64
@@ -346,39 +359,79 @@ __device__ __forceinline__ bool accept_bits(long long ub, double h) {
   return hb <= 0x7ff0000000000000ll && ub < hb;
 }
 
-constexpr int kRejectThreads = 512;
-constexpr int kLeadWarps = 4;
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
 
-__global__ void __launch_bounds__(kRejectThreads) k_reject(
-    DevState* st, const double* __restrict__ H, const double* __restrict__ uprop,
-    const double* __restrict__ uacc, const int* __restrict__ prop, double* Lw, double* L, int ldL,
-    int* Sacc, long long* piv, double* Hglobal, int use_smem) {
-  extern __shared__ double dyn[];
+__device__ __forceinline__ uint32_t map_to(const void* p, uint32_t cta) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(out)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(cta));
+  return out;
+}
+
+__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThreads)
+    k_reject(DevState* st, const double* __restrict__ H, const double* __restrict__ uprop,
+             const double* __restrict__ uacc, const int* __restrict__ prop, double* Lw, double* L,
+             int ldL, int* Sacc, long long* piv, int fp64) {
+  extern __shared__ double Hown[];  // packed rows owned by this CTA (CTAs 1..)
   __shared__ double lcb[2][kTMax];  // column of accepted pivot t in lcb[t & 1]
-  __shared__ double dg[kTMax];      // current Schur diagonal
-  __shared__ long long ub[kTMax];   // u_i U_i, bit pattern of a non-negative double
+  __shared__ double dg[kTMax];      // lead CTA: current Schur diagonal
+  __shared__ long long ub[kTMax];   // lead CTA: u_i U_i, bit pattern of a non-negative double
   __shared__ int accl[kTMax];
   __shared__ int nxt_sh[2];
   __shared__ double inv_sh[2];
+  // every CTA of the cluster reads the same state, so all take the same path
   if (st->done) return;
   const int T = st->T;
   const long long rank = st->rank;
   long long maxacc_ll = st->k - rank;
   const int maxacc = maxacc_ll < T ? (int)maxacc_ll : T;
-  double* Hp = use_smem ? dyn : Hglobal;
+  const uint32_t cr = cluster_rank();
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int j = warp; j < T; j += nw)
-    for (int l = lane; l <= j; l += 32) Hp[pk(j, l)] = H[(long long)j * T + l];
-  for (int i = tid; i < T; i += nt) {
-    dg[i] = H[(long long)i * T + i];
-    const long long u = __double_as_longlong(uprop[i] * uacc[i]);
-    ub[i] = u < 0 ? 0 : u;  // -0 -> +0
-    lcb[1][i] = 0.0;        // "column -1": no downdate before pivot 0
+  const bool lead = cr == 0;
+  const int own = (int)cr - 1;  // owner index of the rows of this CTA (CTAs 1..)
+
+  if (lead) {
+    for (int i = tid; i < T; i += nt) {
+      dg[i] = H[(long long)i * T + i];
+      const long long u = __double_as_longlong(uprop[i] * uacc[i]);
+      ub[i] = u < 0 ? 0 : u;  // -0 -> +0
+      lcb[1][i] = 0.0;        // "column -1": no downdate before pivot 0
+    }
+  } else {
+    // rows j = own + kRejOwners i, one warp per row
+    for (int j = own + kRejOwners * warp; j < T; j += kRejOwners * nw) {
+      const int o = own_off(j);
+      for (int l = lane; l <= j; l += 32) Hown[o + l] = H[(long long)j * T + l];
+    }
   }
   __syncthreads();
 
-  // first acceptance at or after i0 (warp 0), T if none
+  // first acceptance at or after i0 (lead warp 0), T if none
   auto next_accept = [&](int i0) -> int {
     for (int c = i0; c < T; c += 32) {
       const int i = c + lane;
@@ -387,121 +440,124 @@ __global__ void __launch_bounds__(kRejectThreads) k_reject(
     }
     return T;
   };
-  if (warp == 0) {
+  // the next pivot, to every CTA of the cluster
+  auto publish = [&](int slot, int nx, double iv) {
+    nxt_sh[slot] = nx;
+    inv_sh[slot] = iv;
+    for (int c = 1; c < kRejCluster; ++c) st_cluster_s32(map_to(&nxt_sh[slot], c), nx);
+  };
+  if (lead && warp == 0) {
     const int nx = maxacc > 0 ? next_accept(0) : T;
-    if (lane == 0) {
-      nxt_sh[0] = nx;
-      inv_sh[0] = nx < T ? rsqrt_newton(dg[nx]) : 0.0;
-    }
+    if (lane == 0) publish(0, nx, nx < T ? rsqrt_newton(dg[nx], fp64) : 0.0);
   }
-  __syncthreads();
+  cluster_sync_all();
 
   int t = 0;
   for (;; ++t) {
     const int n_t = nxt_sh[t & 1];
     if (n_t >= T) break;
     const double* lp = lcb[(t + 1) & 1];  // column of pivot t - 1
-    if (warp < kLeadWarps) {
-      const double inv = inv_sh[t & 1];
-      const double lpn = lp[n_t];
-      double* lc = lcb[t & 1];
-      // column t below the pivot; warp 0 owns rows n_t+1..n_t+32, the ones
-      // the next acceptance test looks at first
-      double dwin = 0.0;
-      for (int j = n_t + 1 + tid; j < T; j += 32 * kLeadWarps) {
-        const double v = fma(-lp[j], lpn, Hp[pk(j, n_t)]) * inv;
-        lc[j] = v;
-        Lw[(long long)j * kTMax + t] = v;
-        const double dn = fma(-v, v, dg[j]);
-        dg[j] = dn;
-        if (j < n_t + 1 + 32 * kLeadWarps) dwin = dn;
-      }
-      if (tid == 32 * kLeadWarps - 1) {  // the pivot's own entry, h / sqrt(h)
-        const double v = fma(-lpn, lpn, Hp[pk(n_t, n_t)]) * inv;
-        lc[n_t] = v;
-        Lw[(long long)n_t * kTMax + t] = v;
-      }
-      if (warp == 0) {
-        // the next acceptance from warp 0's own rows when there is one there,
-        // without waiting for the other lead warps
-        int nx = T;
-        bool waited = false;
-        double hx = 0.0;
-        if (t + 1 < maxacc) {
-          const int i = n_t + 1 + lane;
-          const unsigned m = __ballot_sync(0xffffffffu, i < T && accept_bits(ub[i], dwin));
-          if (m) {
-            const int src = __ffs(m) - 1;
-            nx = n_t + 1 + src;
-            hx = __shfl_sync(0xffffffffu, dwin, src);
-          } else {
-            asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
-            waited = true;
-            nx = next_accept(n_t + 33);
-            if (nx < T) hx = dg[nx];
+    if (lead) {
+      if (warp < kLeadWarps) {
+        const double inv = inv_sh[t & 1];
+        const double lpn = lp[n_t];
+        double* lc = lcb[t & 1];
+        // column t below the pivot; warp 0 owns rows n_t+1..n_t+32, the ones
+        // the next acceptance test looks at first
+        double dwin = 0.0;
+        for (int j = n_t + 1 + tid; j < T; j += 32 * kLeadWarps) {
+          const int oc = 1 + j % kRejOwners;
+          const double h = ld_cluster_f64(map_to(Hown + own_off(j) + n_t, oc));
+          const double v = fma(-lp[j], lpn, h) * inv;
+          lc[j] = v;
+          Lw[(long long)j * kTMax + t] = v;
+          for (int c = 1; c < kRejCluster; ++c) st_cluster_f64(map_to(&lcb[t & 1][j], c), v);
+          const double dn = fma(-v, v, dg[j]);
+          dg[j] = dn;
+          if (j < n_t + 1 + 32 * kLeadWarps) dwin = dn;
+        }
+        if (tid == 32 * kLeadWarps - 1) {  // the pivot's own entry, h / sqrt(h)
+          const double h = ld_cluster_f64(map_to(Hown + own_off(n_t) + n_t, 1 + n_t % kRejOwners));
+          const double v = fma(-lpn, lpn, h) * inv;
+          lc[n_t] = v;
+          Lw[(long long)n_t * kTMax + t] = v;
+        }
+        if (warp == 0) {
+          int nx = T;
+          bool waited = false;
+          double hx = 0.0;
+          if (t + 1 < maxacc) {
+            const int i = n_t + 1 + lane;
+            const unsigned m = __ballot_sync(0xffffffffu, i < T && accept_bits(ub[i], dwin));
+            if (m) {
+              const int src = __ffs(m) - 1;
+              nx = n_t + 1 + src;
+              hx = __shfl_sync(0xffffffffu, dwin, src);
+            } else {
+              asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+              waited = true;
+              nx = next_accept(n_t + 33);
+              if (nx < T) hx = dg[nx];
+            }
           }
+          if (lane == 0) {
+            publish((t + 1) & 1, nx, nx < T ? rsqrt_newton(hx, fp64) : 0.0);
+            accl[t] = n_t;
+          }
+          if (!waited) asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+        } else {
+          asm volatile("bar.arrive 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
         }
-        if (lane == 0) {
-          nxt_sh[(t + 1) & 1] = nx;
-          inv_sh[(t + 1) & 1] = nx < T ? rsqrt_newton(hx) : 0.0;
-          accl[t] = n_t;
-        }
-        if (!waited) asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
-      } else {
-        asm volatile("bar.arrive 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
       }
-    } else if (t > 0 && (warp & 3) != 0) {
-      // downdate of pivot t - 1 on rows and columns base..T-1: row base + r
-      // is paired with row base + m - 1 - r, m + 1 entries together.  Warps
-      // 4, 8, 12 stay idle: they share warp 0's scheduler (warp w issues on
-      // sub-partition w mod 4), whose FP64 pipe is kept for the lead chain.
-      const int base = n_t + 1, m = T - base;
-      const int tw = (warp >> 2) * 3 + (warp & 3) - 4;
-      const int ntw = (nw >> 2) * 3 - 3;
-      for (int r = tw; r < (m + 1) / 2; r += ntw) {
-        const int ra = base + r, rb = base + m - 1 - r;
-        const int lenA = r + 1;
-        const int tot = ra == rb ? lenA : m + 1;
-        for (int q = lane; q < tot; q += 32) {
-          const int j = q < lenA ? ra : rb;
-          const int l = base + (q < lenA ? q : q - lenA);
-          const long long o = pk(j, l);
-          Hp[o] = fma(-lp[j], lp[l], Hp[o]);
-        }
+    } else if (t > 0) {
+      // downdate of pivot t - 1 on this CTA's rows j > n_t, columns n_t < l <= j
+      int i0 = (n_t + 1 - own + kRejOwners - 1) / kRejOwners;  // first owned row > n_t
+      if (i0 < 0) i0 = 0;
+      for (int j = own + kRejOwners * (i0 + warp); j < T; j += kRejOwners * nw) {
+        const int o = own_off(j);
+        const double lj = lp[j];
+        for (int l = n_t + 1 + lane; l <= j; l += 32) Hown[o + l] = fma(-lj, lp[l], Hown[o + l]);
       }
     }
+    cluster_sync_all();
+  }
+  if (lead) {
+    const int n = t;
+    for (int e = tid; e < n * n; e += nt) {
+      const int a = e / n, c = e % n;
+      L[(long long)a * ldL + c] = c <= a ? Lw[(long long)accl[a] * kTMax + c] : 0.0;
+    }
+    for (int a = tid; a < n; a += nt) {
+      const int p = prop[accl[a]];
+      Sacc[a] = p;
+      piv[rank + a] = p;
+    }
     __syncthreads();
-  }
-  const int n = t;
-  for (int e = tid; e < n * n; e += nt) {
-    const int a = e / n, c = e % n;
-    L[(long long)a * ldL + c] = c <= a ? Lw[(long long)accl[a] * kTMax + c] : 0.0;
-  }
-  for (int a = tid; a < n; a += nt) {
-    const int p = prop[accl[a]];
-    Sacc[a] = p;
-    piv[rank + a] = p;
-  }
-  if (tid == 0) {
-    st->s = n;
-    if (n > 0 && !(L[0] > 0.0)) st->status |= kStNumeric;
+    if (tid == 0) {
+      st->s = n;
+      if (n > 0 && !(L[0] > 0.0)) st->status |= kStNumeric;
+    }
   }
 }
 
 cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s) {
-  const size_t packed = (size_t)T * (T + 1) / 2 * sizeof(double);
-  const size_t static_bytes = sizeof(double) * 4 * kTMax + sizeof(long long) * kTMax +
-                              sizeof(int) * kTMax + 64;
-  const size_t limit = 227 * 1024 - static_bytes - 1024;
-  const int use_smem = packed <= limit ? 1 : 0;
-  const size_t dyn = use_smem ? packed : 0;
-  if (use_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)dyn);
-    if (e != cudaSuccess) return e;
+  // packed rows of the CTA that owns the most
+  size_t most = 0;
+  for (int o = 0; o < kRejOwners; ++o) {
+    size_t n = 0;
+    for (int j = o; j < T; j += kRejOwners) n += (size_t)j + 1;
+    if (n > most) most = n;
   }
-  k_reject<<<1, kRejectThreads, dyn, s>>>(b.st, b.H, b.uprop, b.uacc, b.prop, b.Lw, b.L, b.Tmax,
-                                          b.Sacc, b.piv, b.Hpk, use_smem);
+  const size_t dyn = most * sizeof(double);
+  static size_t attr = 0;
+  if (dyn > 48 * 1024 && dyn > attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    attr = dyn;
+  }
+  k_reject<<<kRejCluster, kRejectThreads, dyn, s>>>(b.st, b.H, b.uprop, b.uacc, b.prop, b.Lw,
+                                                    b.L, b.Tmax, b.Sacc, b.piv, b.mixed ? 0 : 1);
   return cudaGetLastError();
 }
 

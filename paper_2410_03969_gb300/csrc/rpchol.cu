@@ -451,7 +451,6 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   ALLOC(L, double, (size_t)kTMax * T_max);
   ALLOC(Linv, double, (size_t)kTMax * T_max);
   ALLOC(Sacc, int, kTMax);
-  ALLOC(Hpk, double, (size_t)kTMax * (kTMax + 1) / 2);
   ALLOC(Hpart, double, (size_t)kHTilesMax * kHSplitMax * 256);
   ALLOC(hcnt, int, kHTilesMax);
   ALLOC(red, double, b.nred);
