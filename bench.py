@@ -112,6 +112,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_throughput(local_ms, steps, k, world, device):
+    """Whole-job pivots/s: every rank factorises `steps` problems to rank k;
+    the job takes as long as its slowest rank (max over ranks of the timed
+    region).  Returns (max_ms, pivots per second over all ranks)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * k / (total_ms / 1e3)
+
+
 def _problem(args):
     """The workload; --n-points shrinks N (small cases for profiling only)."""
     make = workloads.WORKLOADS[args.workload]
@@ -243,12 +257,8 @@ def ours_arm(args):
     mean_rounds = sum(rounds) / len(rounds)
     launches = int(round(args.steps * sum(kl) / len(kl)))
 
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = job_throughput(total_ms, args.steps, k, world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * args.steps * k / (total_ms / 1e3)
 
     extra = {}
     if rank == 0 and not args.quick:

@@ -113,21 +113,112 @@ __device__ __forceinline__ void store16(float* dst, const float* v, int ncols, i
   }
 }
 
-// acc[jj] += sum_m x[m] W(l0 + m, jj), W rows of 16 floats
+// acc[jj] += sum_m x[m] W(m, jj), W rows of 16 floats; the 16 sums are
+// kept as 8 pairs and updated with the packed two-lane FP32 FMA.
 template <int M>
-__device__ __forceinline__ void fma_rows(float* acc, const float* x, const float* W) {
+__device__ __forceinline__ void fma_rows(float2* acc, const float* x, const float* W) {
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const float xv = x[m];
+    const float2 xv = make_float2(x[m], x[m]);
     const float4* wr = (const float4*)(W + 16 * m);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const float4 w = wr[g];
-      acc[4 * g] = fmaf(xv, w.x, acc[4 * g]);
-      acc[4 * g + 1] = fmaf(xv, w.y, acc[4 * g + 1]);
-      acc[4 * g + 2] = fmaf(xv, w.z, acc[4 * g + 2]);
-      acc[4 * g + 3] = fmaf(xv, w.w, acc[4 * g + 3]);
+      acc[2 * g] = __ffma2_rn(xv, make_float2(w.x, w.y), acc[2 * g]);
+      acc[2 * g + 1] = __ffma2_rn(xv, make_float2(w.z, w.w), acc[2 * g + 1]);
     }
+  }
+}
+// One tile row's share of the epilogue: what the block loop needs.
+struct EpiRow {
+  uint32_t d1, d2;      // TMEM addresses of this row's D1 and D2 (column 0)
+  const float* W;       // W blocks of the round (shared or global memory)
+  const float* nrmSs;   // squared norms of the round's pivots
+  const double* L;      // FP64 Cholesky factor of the round, row jpiv
+  float* frow;          // F(row, rank), nullptr beyond N
+  int s, nF, jpiv, mis, kind, ldL;
+  float nr, inv_sigma;
+};
+
+// Block bi of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2, from TMEM.
+__device__ __forceinline__ void r_block(const EpiRow& e, int bi, float* v1) {
+  const int j0 = 16 * bi;
+  float v2[16];
+  if (e.nF > 0) {
+    tc::tmem_ld16x2_sync(e.d1 + j0, e.d2 + j0, v1, v2);
+  } else {
+    tc::tmem_ld16_sync(e.d1 + j0, v1);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v2[m] = 0.f;
+  }
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const int c = j0 + m;
+    const float kv =
+        c == e.jpiv ? 1.f : phi_r2<float>(e.kind, e.inv_sigma, e.nr + e.nrmSs[c] - 2.f * v1[m]);
+    v1[m] = c < e.s ? kv - v2[m] : 0.f;
+  }
+}
+
+// Block bi of G is final: pivot-row override, store to F, sum of squares.
+__device__ __forceinline__ void g_block_out(const EpiRow& e, int bi, const float2* acc2,
+                                            float* acc, float& rsq, float& rc) {
+  const int j0 = 16 * bi;
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    acc[2 * jj] = acc2[jj].x;
+    acc[2 * jj + 1] = acc2[jj].y;
+  }
+  if (e.jpiv >= 0) {
+    // A pivot row of this round: in exact arithmetic R(S,:) = L L^*, so
+    // G(S_j,:) = L(j,:) and its residual is zero.  The exact values (L from
+    // the FP64 Cholesky of H) replace the rounded contraction, so a chosen
+    // pivot keeps zero proposal weight and its row of F agrees with the H
+    // that later rounds form from it.
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int c = j0 + jj;
+      acc[jj] = (c < e.s && c <= e.jpiv) ? (float)e.L[(long long)e.jpiv * e.ldL + c] : 0.f;
+    }
+  }
+  if (e.frow) store16(e.frow + j0, acc, e.s - j0, e.mis);
+  float bs = 0.f;
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) bs = fmaf(acc[jj], acc[jj], bs);
+  const float y = bs - rc;
+  const float t = rsq + y;
+  rc = (t - rsq) - y;
+  rsq = t;
+}
+
+// G L^* = R by blocks of 16 columns,
+//   G_b = sum_{l < j0} G(:, l) W_b(l, :) + sum_m R(:, j0 + m) W_b(j0 + m, :),
+// with the finished blocks of G stored back into TMEM over the consumed D1
+// blocks and read from there.
+__device__ __forceinline__ void epi_row_tmem(const EpiRow& e, int nblk, float& rsq, float& rc) {
+  for (int bi = 0; bi < nblk; ++bi) {
+    const float* Wb = e.W + 128 * bi * (bi + 1);
+    float2 acc2[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) acc2[jj] = make_float2(0.f, 0.f);
+    int lb = 0;
+    for (; lb + 1 < bi; lb += 2) {  // two earlier G blocks per TMEM wait
+      float g0[16], g1[16];
+      tc::tmem_ld16x2_sync(e.d1 + 16 * lb, e.d1 + 16 * lb + 16, g0, g1);
+      fma_rows<16>(acc2, g0, Wb + 256 * lb);
+      fma_rows<16>(acc2, g1, Wb + 256 * (lb + 1));
+    }
+    if (lb < bi) {
+      float g0[16];
+      tc::tmem_ld16_sync(e.d1 + 16 * lb, g0);
+      fma_rows<16>(acc2, g0, Wb + 256 * lb);
+    }
+    float v1[16];
+    r_block(e, bi, v1);
+    fma_rows<16>(acc2, v1, Wb + 256 * bi);
+    float acc[16];
+    g_block_out(e, bi, acc2, acc, rsq, rc);
+    tc::tmem_st16_sync(e.d1 + 16 * bi, acc);  // G_b over the consumed D1 block
   }
 }
 }  // namespace
@@ -151,7 +242,6 @@ struct TcArgs {
   int ldL;
 };
 
-template <int KIND>  // kernel map, specialised so the epilogue has one code path
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_colstep_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmX,
                  const __grid_constant__ CUtensorMap tmXlo,
@@ -321,6 +411,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (c >= nX) {
           // a row's 128 bytes are one swizzle row: process them in place in
           // any chunk order (rotated by row to spread the banks)
+          // both rows are read into registers before any store, so that the
+          // loads are not held behind stores the compiler cannot prove apart
+          float4 v[2][8];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = e + 64 * h;
+            const float4* pa = (const float4*)(sm + stg * SB + r * 128);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[h][q] = pa[(q + r) & 7];
+          }
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = e + 64 * h;
@@ -329,11 +429,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int j = (q + r) & 7;
-              const float4 v = pa[j];
-              const float4 hd = make_float4(tc::tf32_head(v.x), tc::tf32_head(v.y),
-                                            tc::tf32_head(v.z), tc::tf32_head(v.w));
+              const float4 x = v[h][q];
+              const float4 hd = make_float4(tc::tf32_head(x.x), tc::tf32_head(x.y),
+                                            tc::tf32_head(x.z), tc::tf32_head(x.w));
               pa[j] = hd;
-              pl[j] = make_float4(v.x - hd.x, v.y - hd.y, v.z - hd.z, v.w - hd.w);
+              pl[j] = make_float4(x.x - hd.x, x.y - hd.y, x.z - hd.z, x.w - hd.w);
             }
           }
           tc::fence_proxy_async_smem();
@@ -377,67 +477,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::tc_fence_after();
       const uint32_t d1 = tbase + lane_off + (uint32_t)((nbuf == 2 ? grp : 0) * 256);
       const uint32_t d2 = d1 + (nbuf == 2 ? 128u : 256u);
-      float* frow = a.F + grow * a.ldF + rank;
+      EpiRow er;
+      er.d1 = d1;
+      er.d2 = d2;
+      er.W = Lo.w_resident ? Wsm : a.W;
+      er.nrmSs = nrmSs;
+      er.L = a.L;
+      er.frow = live ? a.F + grow * a.ldF + rank : nullptr;
+      er.s = s;
+      er.nF = nF;
+      er.jpiv = jpiv;
+      er.mis = mis;
+      er.kind = a.kind;
+      er.ldL = a.ldL;
+      er.nr = nr;
+      er.inv_sigma = a.inv_sigma;
       float rsq = 0.f, rc = 0.f;  // Kahan-compensated sum of G^2 over the row
-      // ---- G L^* = R by blocks of 16 columns:
-      //   G_b = sum_{l < j0} G(:, l) W_b(l, :) + sum_m R(:, j0 + m) W_b(j0 + m, :)
-      for (int bi = 0; bi < nblk; ++bi) {
-        const int j0 = bi * 16;
-        const float* Wb = (Lo.w_resident ? Wsm : a.W) + 128 * bi * (bi + 1);
-        float acc[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) acc[jj] = 0.f;
-        int lb = 0;
-        for (; lb + 1 < bi; lb += 2) {  // two earlier G blocks per TMEM wait
-          float g0[16], g1[16];
-          tc::tmem_ld16x2_sync(d1 + 16 * lb, d1 + 16 * lb + 16, g0, g1);
-          fma_rows<16>(acc, g0, Wb + 256 * lb);
-          fma_rows<16>(acc, g1, Wb + 256 * (lb + 1));
-        }
-        if (lb < bi) {
-          float g0[16];
-          tc::tmem_ld16_sync(d1 + 16 * lb, g0);
-          fma_rows<16>(acc, g0, Wb + 256 * lb);
-        }
-        // this block of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2
-        float v1[16], v2[16];
-        if (nF > 0) {
-          tc::tmem_ld16x2_sync(d1 + j0, d2 + j0, v1, v2);
-        } else {
-          tc::tmem_ld16_sync(d1 + j0, v1);
-#pragma unroll
-          for (int m = 0; m < 16; ++m) v2[m] = 0.f;
-        }
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int c = j0 + m;
-          const float kv = c == jpiv ? 1.f
-                                     : phi_r2<float>(KIND, a.inv_sigma, nr + nrmSs[c] - 2.f * v1[m]);
-          v1[m] = c < s ? kv - v2[m] : 0.f;
-        }
-        fma_rows<16>(acc, v1, Wb + 256 * bi);
-        if (jpiv >= 0) {
-          // A pivot row of this round: in exact arithmetic R(S,:) = L L^*, so
-          // G(S_j,:) = L(j,:) and its residual is zero.  The exact values (L
-          // from the FP64 Cholesky of H) replace the rounded contraction, so a
-          // chosen pivot keeps zero proposal weight and its row of F agrees
-          // with the H that later rounds form from it.
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int c = j0 + jj;
-            acc[jj] = (c < s && c <= jpiv) ? (float)a.L[(long long)jpiv * a.ldL + c] : 0.f;
-          }
-        }
-        tc::tmem_st16_sync(d1 + j0, acc);  // G_b over the consumed D1 block
-        if (live) store16(frow + j0, acc, s - j0, mis);
-        float bs = 0.f;
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) bs = fmaf(acc[jj], acc[jj], bs);
-        const float y = bs - rc;
-        const float t = rsq + y;
-        rc = (t - rsq) - y;
-        rsq = t;
-      }
+      epi_row_tmem(er, nblk, rsq, rc);
       tc::tc_fence_before();
       tc::mbar_arrive_warp(&tfree[nbuf == 2 ? grp : 0]);  // TMEM buffer free for tile it + nbuf
       // ---- residual diagonal (FP64) and the tile's sum of d
@@ -462,14 +518,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_colstep_tc<0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_colstep_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kSmemMax);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_colstep_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_colstep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemMax);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -494,15 +544,7 @@ cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t
   const unsigned grid = (unsigned)(ntiles < m.num_sms ? ntiles : m.num_sms);
   // the shared-memory layout depends on s, which only the device knows: the
   // launch reserves the maximum
-  if (b.kind == 0)
-    k_colstep_tc<0><<<grid, kTcThreads, kSmemMax, s>>>(m.F, m.X, m.Xlo, m.FSh, m.FSl, m.XSh,
-                                                       m.XSl, a);
-  else if (b.kind == 1)
-    k_colstep_tc<1><<<grid, kTcThreads, kSmemMax, s>>>(m.F, m.X, m.Xlo, m.FSh, m.FSl, m.XSh,
-                                                       m.XSl, a);
-  else
-    k_colstep_tc<2><<<grid, kTcThreads, kSmemMax, s>>>(m.F, m.X, m.Xlo, m.FSh, m.FSl, m.XSh,
-                                                       m.XSl, a);
+  k_colstep_tc<<<grid, kTcThreads, kSmemMax, s>>>(m.F, m.X, m.Xlo, m.FSh, m.FSl, m.XSh, m.XSl, a);
   return cudaGetLastError();
 }
 

@@ -387,6 +387,72 @@ __device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
   asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+// Asynchronous store into another CTA's shared memory that completes
+// `bytes` of that CTA's barrier's expected transaction count on arrival.
+__device__ __forceinline__ void st_async_f64(const void* dst, double v, uint64_t* bar,
+                                             uint32_t cta) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(
+          map_to(dst, cta)),
+      "l"(__double_as_longlong(v)), "r"(map_to(bar, cta))
+      : "memory");
+}
+
+__device__ __forceinline__ void st_async_s32(const void* dst, int v, uint64_t* bar,
+                                             uint32_t cta) {
+  asm volatile(
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+          map_to(dst, cta)),
+      "r"(v), "r"(map_to(bar, cta))
+      : "memory");
+}
+
+// This thread's arrival on a barrier of its own CTA, announcing `bytes` of
+// asynchronous stores still to come in the current phase.
+__device__ __forceinline__ void arrive_expect_local(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// mbarrier arrival on a barrier of another CTA of the cluster, releasing
+// this thread's earlier writes (and those ordered before them) cluster-wide
+__device__ __forceinline__ void arrive_remote(uint64_t* bar, uint32_t cta) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                   map_to(bar, cta))
+               : "memory");
+}
+
+// Bounded wait (acquire, cluster scope) for the phase of the given parity of
+// a barrier of this CTA: false once the deadline (ns of %globaltimer) passes.
+__device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t parity,
+                                                     unsigned long long deadline) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  for (uint32_t n = 0;; ++n) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((n & 15) == 15) {
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (now > deadline) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -403,6 +469,8 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
   __shared__ int accl[kTMax];
   __shared__ int nxt_sh[2];
   __shared__ double inv_sh[2];
+  __shared__ __align__(8) uint64_t bars[2];  // lead: teams done; others: column published
+  __shared__ int ok_sh;
   // every CTA of the cluster reads the same state, so all take the same path
   if (st->done) return;
   const int T = st->T;
@@ -414,7 +482,21 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const bool lead = cr == 0;
   const int own = (int)cr - 1;  // owner index of the rows of this CTA (CTAs 1..)
+  constexpr unsigned long long kWait = 2000000000ull;  // 2 s per wait
 
+  if (tid == 0) {
+    const uint32_t cnt = lead ? (uint32_t)kRejOwners : 1u;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&bars[0])),
+                 "r"(cnt)
+                 : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&bars[1])),
+                 "r"(cnt)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!lead) arrive_expect_local(&bars[0], 4u);  // publication 0: n_0 alone
+  }
   if (lead) {
     for (int i = tid; i < T; i += nt) {
       dg[i] = H[(long long)i * T + i];
@@ -429,7 +511,7 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
       for (int l = lane; l <= j; l += 32) Hown[o + l] = H[(long long)j * T + l];
     }
   }
-  __syncthreads();
+  cluster_sync_all();  // rows loaded and barriers initialised in every CTA
 
   // first acceptance at or after i0 (lead warp 0), T if none
   auto next_accept = [&](int i0) -> int {
@@ -440,41 +522,46 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
     }
     return T;
   };
-  // the next pivot, to every CTA of the cluster
-  auto publish = [&](int slot, int nx, double iv) {
-    nxt_sh[slot] = nx;
-    inv_sh[slot] = iv;
-    for (int c = 1; c < kRejCluster; ++c) st_cluster_s32(map_to(&nxt_sh[slot], c), nx);
+  // publication p to every other CTA: column p - 1 (rows beyond n_{p-1},
+  // sent by the lead warps) and n_p (lead warp 0, lane 0), each value an
+  // asynchronous store that counts towards the receiver's barrier phase
+  auto publish = [&](int p, int nx) {
+    for (int c = 1; c < kRejCluster; ++c) st_async_s32(&nxt_sh[p & 1], nx, &bars[p & 1], c);
   };
-  if (lead && warp == 0) {
-    const int nx = maxacc > 0 ? next_accept(0) : T;
-    if (lane == 0) publish(0, nx, nx < T ? rsqrt_newton(dg[nx], fp64) : 0.0);
-  }
-  cluster_sync_all();
 
   int t = 0;
-  for (;; ++t) {
-    const int n_t = nxt_sh[t & 1];
-    if (n_t >= T) break;
-    const double* lp = lcb[(t + 1) & 1];  // column of pivot t - 1
-    if (lead) {
-      if (warp < kLeadWarps) {
+  if (lead) {
+    if (warp < kLeadWarps) {
+      if (warp == 0) {
+        const int nx = maxacc > 0 ? next_accept(0) : T;
+        if (lane == 0) {
+          nxt_sh[0] = nx;
+          inv_sh[0] = nx < T ? rsqrt_newton(dg[nx], fp64) : 0.0;
+          publish(0, nx);
+        }
+      }
+      asm volatile("bar.sync 2, %0;" ::"r"(32 * kLeadWarps) : "memory");
+      for (;; ++t) {
+        const int n_t = nxt_sh[t & 1];
+        if (n_t >= T) break;
+        const double* lp = lcb[(t + 1) & 1];  // column of pivot t - 1
         const double inv = inv_sh[t & 1];
         const double lpn = lp[n_t];
         double* lc = lcb[t & 1];
-        // column t below the pivot; warp 0 owns rows n_t+1..n_t+32, the ones
-        // the next acceptance test looks at first
+        // column t below the pivot, from the rows' owners; warp 0 owns rows
+        // n_t+1..n_t+32, the ones the next acceptance test looks at first
         double dwin = 0.0;
         for (int j = n_t + 1 + tid; j < T; j += 32 * kLeadWarps) {
           const int oc = 1 + j % kRejOwners;
           const double h = ld_cluster_f64(map_to(Hown + own_off(j) + n_t, oc));
           const double v = fma(-lp[j], lpn, h) * inv;
-          lc[j] = v;
-          Lw[(long long)j * kTMax + t] = v;
-          for (int c = 1; c < kRejCluster; ++c) st_cluster_f64(map_to(&lcb[t & 1][j], c), v);
           const double dn = fma(-v, v, dg[j]);
           dg[j] = dn;
           if (j < n_t + 1 + 32 * kLeadWarps) dwin = dn;
+          lc[j] = v;
+          Lw[(long long)j * kTMax + t] = v;
+          for (int c = 1; c < kRejCluster; ++c)
+            st_async_f64(&lcb[t & 1][j], v, &bars[(t + 1) & 1], c);
         }
         if (tid == 32 * kLeadWarps - 1) {  // the pivot's own entry, h / sqrt(h)
           const double h = ld_cluster_f64(map_to(Hown + own_off(n_t) + n_t, 1 + n_t % kRejOwners));
@@ -483,6 +570,8 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
           Lw[(long long)n_t * kTMax + t] = v;
         }
         if (warp == 0) {
+          // barrier 1: the lead warps' parts of column t are out; barrier 2:
+          // warp 0's decision is in nxt_sh / inv_sh
           int nx = T;
           bool waited = false;
           double hx = 0.0;
@@ -500,29 +589,63 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
               if (nx < T) hx = dg[nx];
             }
           }
-          if (lane == 0) {
-            publish((t + 1) & 1, nx, nx < T ? rsqrt_newton(hx, fp64) : 0.0);
-            accl[t] = n_t;
-          }
+          const double iv = nx < T ? rsqrt_newton(hx, fp64) : 0.0;
           if (!waited) asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+          int ok = 1;
+          if (lane == 0) {
+            accl[t] = n_t;
+            publish(t + 1, nx);
+            // the other CTAs' downdate of pivot t - 1 (their iteration t) must be
+            // done before the lead reads column n_{t+1}
+            ok = wait_cluster_bounded(&bars[t & 1], (uint32_t)((t >> 1) & 1), now_ns() + kWait);
+            if (!ok) atomicOr(&st->status, (int)kStTimeout);
+            nxt_sh[(t + 1) & 1] = ok ? nx : T;
+            inv_sh[(t + 1) & 1] = iv;
+          }
+          __syncwarp();
+          asm volatile("bar.arrive 2, %0;" ::"r"(32 * kLeadWarps) : "memory");
         } else {
           asm volatile("bar.arrive 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
+          asm volatile("bar.sync 2, %0;" ::"r"(32 * kLeadWarps) : "memory");
         }
       }
-    } else if (t > 0) {
-      // downdate of pivot t - 1 on this CTA's rows j > n_t, columns n_t < l <= j
-      int i0 = (n_t + 1 - own + kRejOwners - 1) / kRejOwners;  // first owned row > n_t
-      if (i0 < 0) i0 = 0;
-      for (int j = own + kRejOwners * (i0 + warp); j < T; j += kRejOwners * nw) {
-        const int o = own_off(j);
-        const double lj = lp[j];
-        for (int l = n_t + 1 + lane; l <= j; l += 32) Hown[o + l] = fma(-lj, lp[l], Hown[o + l]);
+    }
+  } else {
+    for (;; ++t) {
+      if (tid == 0) ok_sh = wait_cluster_bounded(&bars[t & 1], (uint32_t)((t >> 1) & 1),
+                                                 now_ns() + kWait)
+                                ? 1
+                                : 0;
+      __syncthreads();
+      if (!ok_sh) {
+        if (tid == 0) atomicOr(&st->status, (int)kStTimeout);
+        break;
+      }
+      const int n_t = nxt_sh[t & 1];
+      if (n_t >= T) break;
+      // publication t + 1 brings column t for rows n_t+1..T-1 and n_{t+1}
+      if (tid == 0) arrive_expect_local(&bars[(t + 1) & 1], 8u * (uint32_t)(T - 1 - n_t) + 4u);
+      if (t > 0) {
+        // downdate of pivot t - 1 on this CTA's rows j > n_t, columns n_t < l <= j
+        const double* lp = lcb[(t + 1) & 1];
+        const int i0 = (n_t + 1 - own + kRejOwners - 1) / kRejOwners;  // first owned row > n_t
+        for (int j = own + kRejOwners * (i0 + warp); j < T; j += kRejOwners * nw) {
+          const int o = own_off(j);
+          const double lj = lp[j];
+          for (int l = n_t + 1 + lane; l <= j; l += 32) Hown[o + l] = fma(-lj, lp[l], Hown[o + l]);
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("fence.acq_rel.cluster;" ::: "memory");
+        arrive_remote(&bars[t & 1], 0);
       }
     }
-    cluster_sync_all();
   }
+  if (lead && tid == 0) ok_sh = t;  // pivots accepted (lead warps 4.. never ran the loop)
+  cluster_sync_all();  // no CTA leaves while another may still reach its shared memory
   if (lead) {
-    const int n = t;
+    const int n = ok_sh;
     for (int e = tid; e < n * n; e += nt) {
       const int a = e / n, c = e % n;
       L[(long long)a * ldL + c] = c <= a ? Lw[(long long)accl[a] * kTMax + c] : 0.0;
