@@ -203,8 +203,41 @@ rpchol_status rpchol_trace_error_noalloc(const void* F_dev, int32_t F_dtype, int
                                          int64_t ldF, int64_t rank, double* out_dev,
                                          void* stream);
 
-/* Release everything the context owns.  NULL is accepted. */
+/* Release everything the context owns.  NULL is accepted.  A batch that
+ * holds the context must be destroyed first.                              */
 void rpchol_destroy(rpchol_ctx* ctx);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent factorisations (Algorithm 2 each, arXiv 2410.03969 §3)
+ * in one launch: the batch records one CUDA graph in which every context
+ * has its own branch, a reset kernel followed by a conditional while-loop
+ * over that context's rounds (the loop body is the same kernel sequence
+ * rpchol_run launches).  Branches are independent, so the GPU overlaps the
+ * instances' small kernels (sampler, H, Algorithm 1) with the others'
+ * column steps.  Each context keeps its own buffers and results; after a
+ * batch run, rpchol_stats / rpchol_factor / rpchol_copy_factor* on a
+ * context see that context's run (its stream waits for the batch).
+ * The paper runs one factorisation at a time; it has no batched form.     */
+typedef struct rpchol_batch rpchol_batch;
+
+/* Record the batch graph for n >= 1 contexts (all on the current device)
+ * with block sizes T[i] (1 <= T[i] <= that context's T_max).  The batch
+ * borrows the contexts: destroy it before any of them.  Errors: EINVAL
+ * (n < 1, NULL context, T out of range, a context twice), ENOMEM, ECUDA.  */
+rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int32_t* T,
+                                  rpchol_batch** out);
+
+/* Run every instance once: instance i to rank k[i] (1 <= k[i] <= its
+ * k_max) with Philox seed seeds[i] (the same stream contract as
+ * rpchol_run, so instance i draws exactly what rpchol_run(ctx_i, k[i],
+ * T[i], seeds[i]) draws).  Asynchronous on `stream` (cudaStream_t, NULL =
+ * legacy default stream), which first waits for every context's stream.
+ * Errors: EINVAL, ECUDA.                                                   */
+rpchol_status rpchol_batch_run(rpchol_batch* batch, const int64_t* k, const uint64_t* seeds,
+                               void* stream);
+
+/* Release the batch (not the contexts).  NULL is accepted. */
+void rpchol_batch_destroy(rpchol_batch* batch);
 
 #ifdef __cplusplus
 }

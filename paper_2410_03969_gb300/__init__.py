@@ -76,6 +76,16 @@ _SIGNATURES = [
                                               ctypes.c_void_p]),
     ("rpchol_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RunStats)]),
     ("rpchol_destroy", None, [ctypes.c_void_p]),
+    ("rpchol_trace_error_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                                  ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.c_int64, ctypes.c_void_p,
+                                                  ctypes.c_void_p]),
+    ("rpchol_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    ("rpchol_batch_run", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]),
+    ("rpchol_batch_destroy", None, [ctypes.c_void_p]),
 ]
 
 
@@ -264,6 +274,48 @@ class Factorizer:
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().rpchol_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Several Factorizers run together in one launch (one CUDA graph with a
+    conditional round loop per instance); instance i uses block size T[i].
+    Destroy (close) the batch before its factorizers."""
+
+    def __init__(self, factorizers, T):
+        self.members = list(factorizers)
+        n = len(self.members)
+        ctxs = (ctypes.c_void_p * n)(*[f._ctx.value for f in self.members])
+        Ts = (ctypes.c_int32 * n)(*[int(t) for t in T])
+        self._b = ctypes.c_void_p()
+        _check(lib().rpchol_batch_create(ctxs, n, Ts, ctypes.byref(self._b)),
+               "rpchol_batch_create")
+        self.T = [int(t) for t in T]
+
+    def run(self, k, seeds, stream=None):
+        n = len(self.members)
+        ks = (ctypes.c_int64 * n)(*[int(v) for v in k])
+        ss = (ctypes.c_uint64 * n)(*[int(v) & (2**64 - 1) for v in seeds])
+        _check(lib().rpchol_batch_run(self._b, ks, ss,
+                                      stream if stream is not None else _current_stream()),
+               "rpchol_batch_run")
+        return self
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            lib().rpchol_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -50,6 +50,18 @@ struct DevState {
   double col_flops;      // algorithmic flops of the column-step kernels so far
 };
 
+// Parameters of one run, read by the reset kernel of a batched launch (so
+// that one recorded graph serves every run of the batch).
+struct RunParams {
+  long long k;           // target rank
+  long long max_rounds;  // round limit
+  unsigned long long seed;
+  int T;                 // proposals per round
+  int plain;             // 1: simple RPCholesky
+  unsigned instance;     // Philox counter word 3
+  int pad;
+};
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
 // (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,

@@ -77,6 +77,9 @@ void set_last_error(const char* fmt, ...);
 // Round kernels (k_round.cu)
 cudaError_t launch_reset(const DevBuffers& b, long long k, int T, unsigned long long seed,
                          unsigned inst, int plain, long long max_rounds, cudaStream_t s);
+// reset kernel reading its run parameters from device memory, as a node of g
+cudaError_t add_reset_params_node(cudaGraph_t g, const DevBuffers& b, const RunParams* p,
+                                  cudaGraphNode_t* out);
 cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s);

@@ -11,9 +11,10 @@ namespace rpchol {
 // ------------------------------------------------------------------ reset
 // d = diag A = phi(0) = 1 for every kernel here; tile sums are the tile row
 // counts; state initialised for a new run.
-__global__ void k_reset(DevState* st, double* dvec, double* tile_sums, long long N,
-                        long long ntiles, long long k, int T, unsigned long long seed,
-                        unsigned inst, int plain, long long max_rounds) {
+__device__ __forceinline__ void reset_run(DevState* st, double* dvec, double* tile_sums,
+                                          long long N, long long ntiles, long long k, int T,
+                                          unsigned long long seed, unsigned inst, int plain,
+                                          long long max_rounds) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long r = i; r < N; r += stride) dvec[r] = 1.0;
@@ -43,14 +44,49 @@ __global__ void k_reset(DevState* st, double* dvec, double* tile_sums, long long
   }
 }
 
-cudaError_t launch_reset(const DevBuffers& b, long long k, int T, unsigned long long seed,
-                         unsigned inst, int plain, long long max_rounds, cudaStream_t s) {
+__global__ void k_reset(DevState* st, double* dvec, double* tile_sums, long long N,
+                        long long ntiles, long long k, int T, unsigned long long seed,
+                        unsigned inst, int plain, long long max_rounds) {
+  reset_run(st, dvec, tile_sums, N, ntiles, k, T, seed, inst, plain, max_rounds);
+}
+
+__global__ void k_reset_params(DevState* st, double* dvec, double* tile_sums, long long N,
+                               long long ntiles, const RunParams* p) {
+  reset_run(st, dvec, tile_sums, N, ntiles, p->k, p->T, p->seed, p->instance, p->plain,
+            p->max_rounds);
+}
+
+namespace {
+unsigned reset_blocks(const DevBuffers& b) {
   long long blocks = (b.N + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_reset<<<(unsigned)blocks, 256, 0, s>>>(b.st, b.dvec, b.tile_sums, b.N, b.ntiles, k, T, seed,
-                                           inst, plain, max_rounds);
+  return (unsigned)blocks;
+}
+}  // namespace
+
+cudaError_t launch_reset(const DevBuffers& b, long long k, int T, unsigned long long seed,
+                         unsigned inst, int plain, long long max_rounds, cudaStream_t s) {
+  k_reset<<<reset_blocks(b), 256, 0, s>>>(b.st, b.dvec, b.tile_sums, b.N, b.ntiles, k, T, seed,
+                                          inst, plain, max_rounds);
   return cudaGetLastError();
+}
+
+cudaError_t add_reset_params_node(cudaGraph_t g, const DevBuffers& b, const RunParams* p,
+                                  cudaGraphNode_t* out) {
+  DevState* st = b.st;
+  double* dvec = b.dvec;
+  double* ts = b.tile_sums;
+  long long N = b.N, ntiles = b.ntiles;
+  void* args[] = {&st, &dvec, &ts, &N, &ntiles, (void*)&p};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void*)k_reset_params;
+  kp.gridDim = dim3(reset_blocks(b));
+  kp.blockDim = dim3(256);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(out, g, nullptr, 0, &kp);
 }
 
 // ------------------------------------------------------------------ sampler

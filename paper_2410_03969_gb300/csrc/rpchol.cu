@@ -685,3 +685,166 @@ void rpchol_destroy(rpchol_ctx* c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct rpchol_batch {
+  std::vector<rpchol_ctx*> ctxs;
+  std::vector<int> T;
+  std::vector<cudaEvent_t> ready;  // per context: its stream's work so far
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  RunParams* dparams = nullptr;    // device, one per instance
+  RunParams* hparams = nullptr;    // pinned staging
+  cudaEvent_t copied = nullptr;    // staging copy of the last run done
+  cudaEvent_t done = nullptr;      // last batch run done
+  cudaStream_t cap = nullptr;      // private stream used only to record
+  bool ran = false;
+};
+
+namespace {
+
+void batch_release(rpchol_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->ready) cudaEventDestroy(e);
+  if (b->copied) cudaEventSynchronize(b->copied), cudaEventDestroy(b->copied);
+  if (b->done) cudaEventSynchronize(b->done), cudaEventDestroy(b->done);
+  if (b->dparams) cudaFree(b->dparams);
+  if (b->hparams) cudaFreeHost(b->hparams);
+  if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+rpchol_status batch_record(rpchol_batch* b) {
+  const int n = (int)b->ctxs.size();
+  CU(cudaGraphCreate(&b->graph, 0));
+  for (int i = 0; i < n; ++i) {
+    rpchol_ctx* c = b->ctxs[i];
+    cudaGraphNode_t reset;
+    CU(add_reset_params_node(b->graph, c->b, b->dparams + i, &reset));
+    cudaGraphConditionalHandle h;
+    CU(cudaGraphConditionalHandleCreate(&h, b->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(cudaGraphAddNode(&node, b->graph, &reset, nullptr, 1, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    CU(cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    cudaError_t le = launch_body(c, 0, b->T[i], (unsigned long long)h, 1, b->cap);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->cap, &captured);
+    if (le != cudaSuccess) return cuda_fail(le, "capture of a batch branch");
+    if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+  }
+  CU(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return RPCHOL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int32_t* T,
+                                  rpchol_batch** out) {
+  g_err[0] = 0;
+  if (!out || !ctxs || !T || n < 1) {
+    set_err("invalid argument: n=%d", n);
+    return RPCHOL_EINVAL;
+  }
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || T[i] < 1 || T[i] > ctxs[i]->b.Tmax) {
+      set_err("invalid batch member %d (T=%d)", i, T[i]);
+      return RPCHOL_EINVAL;
+    }
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) {
+        set_err("context %d appears twice in the batch", i);
+        return RPCHOL_EINVAL;
+      }
+  }
+  rpchol_batch* b = new (std::nothrow) rpchol_batch();
+  if (!b) {
+    set_err("host allocation failed");
+    return RPCHOL_ENOMEM;
+  }
+  b->ctxs.assign(ctxs, ctxs + n);
+  b->T.assign(T, T + n);
+  auto fail = [&](rpchol_status s) {
+    batch_release(b);
+    delete b;
+    return s;
+  };
+  cudaError_t e = cudaMalloc((void**)&b->dparams, sizeof(RunParams) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->hparams, sizeof(RunParams) * (size_t)n);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ready.push_back(ev);
+  }
+  if (e != cudaSuccess) return fail(cuda_fail(e, "batch setup"));
+  rpchol_status rs = batch_record(b);
+  if (rs != RPCHOL_OK) return fail(rs);
+  *out = b;
+  return RPCHOL_OK;
+}
+
+rpchol_status rpchol_batch_run(rpchol_batch* b, const int64_t* k, const uint64_t* seeds,
+                               void* stream) {
+  g_err[0] = 0;
+  if (!b || !k || !seeds) {
+    set_err("invalid argument");
+    return RPCHOL_EINVAL;
+  }
+  const int n = (int)b->ctxs.size();
+  for (int i = 0; i < n; ++i)
+    if (k[i] < 1 || k[i] > b->ctxs[i]->k_max) {
+      set_err("invalid k=%lld for batch member %d", (long long)k[i], i);
+      return RPCHOL_EINVAL;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b->ran) CU(cudaEventSynchronize(b->copied));  // staging buffer free again
+  for (int i = 0; i < n; ++i) {
+    RunParams& p = b->hparams[i];
+    p.k = k[i];
+    p.max_rounds = 4 * k[i] + 64;
+    p.seed = seeds[i];
+    p.T = b->T[i];
+    p.plain = 0;
+    p.instance = b->ctxs[i]->instance;
+    p.pad = 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    rpchol_ctx* c = b->ctxs[i];
+    CU(cudaEventRecord(b->ready[i], c->stream));
+    CU(cudaStreamWaitEvent(s, b->ready[i], 0));
+  }
+  CU(cudaMemcpyAsync(b->dparams, b->hparams, sizeof(RunParams) * (size_t)n,
+                     cudaMemcpyHostToDevice, s));
+  CU(cudaEventRecord(b->copied, s));
+  CU(cudaGraphLaunch(b->exec, s));
+  CU(cudaEventRecord(b->done, s));
+  for (int i = 0; i < n; ++i) {
+    rpchol_ctx* c = b->ctxs[i];
+    clear_prof(c);
+    c->last_plain = 0;
+    c->has_run = 1;
+    c->host_iters = -1;
+    CU(cudaStreamWaitEvent(c->stream, b->done, 0));
+  }
+  b->ran = true;
+  return RPCHOL_OK;
+}
+
+void rpchol_batch_destroy(rpchol_batch* b) {
+  if (!b) return;
+  batch_release(b);
+  delete b;
+}
+
+}  // extern "C"
