@@ -239,6 +239,79 @@ rpchol_status rpchol_batch_run(rpchol_batch* batch, const int64_t* k, const uint
 /* Release the batch (not the contexts).  NULL is accepted. */
 void rpchol_batch_destroy(rpchol_batch* batch);
 
+/* Device memory (bytes) a context of these sizes allocates: F, the points
+ * and their TF32 planes (mixed mode), d, and the round work arrays.       */
+int64_t rpchol_context_bytes(int64_t N, int32_t d, int64_t k_max, int32_t T_max,
+                             int32_t precision);
+
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching server for factorisation jobs (Algorithm 2 each)
+ * of different N, d, kernel and k.  Jobs queue in arrival order; a worker
+ * thread admits the oldest waiting job as soon as the device memory it
+ * needs (rpchol_context_bytes) fits in the budget next to the jobs that hold
+ * memory and a slot is free, gives it its own context and stream, and
+ * launches its run, so that jobs admitted while others run overlap on the
+ * GPU.  A finished job keeps its factor on the device (and its memory in
+ * the budget) until it is released.  Results do not depend on what else
+ * runs: each job is computed exactly as rpchol_run computes it alone.
+ * The paper has no serving layer.                                          */
+typedef struct rpchol_server rpchol_server;
+
+typedef struct {
+    int32_t kind;        /* rpchol_kernel_kind */
+    double sigma;        /* bandwidth, > 0 */
+    const void* X;       /* host points, N x d row-major; copied by submit */
+    int64_t N;
+    int32_t d;
+    int32_t x_dtype;     /* RPCHOL_DT_F32 or RPCHOL_DT_F64 */
+    int64_t k;           /* target rank, 1 <= k <= N */
+    int32_t T;           /* block size, 0 = 120 (or N if smaller) */
+    int32_t precision;   /* RPCHOL_FP64 or RPCHOL_MIXED */
+    uint64_t seed;       /* Philox seed (same contract as rpchol_run) */
+} rpchol_job;
+
+typedef struct {
+    int32_t state;       /* 0 waiting, 1 running, 2 finished, 3 failed */
+    int32_t status;      /* rpchol_status of the job once finished or failed */
+    int64_t rank;
+    int64_t rounds;
+    double trace_error;  /* tr(A - F F^*) / tr(A) */
+    double queue_ms;     /* submit -> admitted */
+    double run_ms;       /* admitted -> device work observed finished */
+    double latency_ms;   /* submit -> finished */
+    int64_t device_bytes;
+} rpchol_job_result;
+
+/* Start a server on the current device with a device-memory budget (bytes,
+ * > 0) and at most max_slots jobs holding memory at once (>= 1).  Errors:
+ * EINVAL, ECUDA.                                                           */
+rpchol_status rpchol_server_create(int64_t mem_budget_bytes, int32_t max_slots,
+                                   rpchol_server** out);
+
+/* Queue a job; returns its ticket.  X is copied before this returns.
+ * Errors: EINVAL (bad job, or a job that can never fit the budget),
+ * ENOMEM (host copy).                                                      */
+rpchol_status rpchol_server_submit(rpchol_server* srv, const rpchol_job* job, uint64_t* ticket);
+
+/* State and timings of a job; waits up to wait_ms milliseconds (0: no
+ * wait, < 0: until finished) for it to finish.  EINVAL for an unknown or
+ * released ticket.                                                         */
+rpchol_status rpchol_server_poll(rpchol_server* srv, uint64_t ticket, int32_t wait_ms,
+                                 rpchol_job_result* out);
+
+/* Copy a finished job's factor (stored dtype: FP32 in MIXED, FP64 in
+ * FP64 mode; N x ld_out, ld_out >= rank) and pivots to caller memory
+ * (either pointer may be NULL).  EBUSY if the job has not finished.        */
+rpchol_status rpchol_server_copy_factor(rpchol_server* srv, uint64_t ticket, void* F_out,
+                                        int64_t ld_out, int64_t* pivots_out);
+
+/* Free a finished job's device memory (its result is gone afterwards).
+ * EBUSY if the job has not finished.                                       */
+rpchol_status rpchol_server_release(rpchol_server* srv, uint64_t ticket);
+
+/* Stop the worker, wait for running jobs, free everything. */
+void rpchol_server_destroy(rpchol_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

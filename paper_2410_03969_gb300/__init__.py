@@ -86,6 +86,19 @@ _SIGNATURES = [
     ("rpchol_batch_run", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]),
     ("rpchol_batch_destroy", None, [ctypes.c_void_p]),
+    ("rpchol_context_bytes", ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.c_int32, ctypes.c_int32]),
+    ("rpchol_server_create", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    ("rpchol_server_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_uint64)]),
+    ("rpchol_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                          ctypes.c_void_p]),
+    ("rpchol_server_copy_factor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                                 ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_void_p]),
+    ("rpchol_server_release", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("rpchol_server_destroy", None, [ctypes.c_void_p]),
 ]
 
 
@@ -316,6 +329,87 @@ class Batch:
         if getattr(self, "_b", None) and self._b.value:
             lib().rpchol_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("sigma", ctypes.c_double), ("X", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("d", ctypes.c_int32), ("x_dtype", ctypes.c_int32),
+                ("k", ctypes.c_int64), ("T", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("rank", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("trace_error", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+JOB_STATES = ("waiting", "running", "finished", "failed")
+
+
+def context_bytes(N: int, d: int, k_max: int, T_max: int, precision: str = "mixed") -> int:
+    return int(lib().rpchol_context_bytes(int(N), int(d), int(k_max), int(T_max),
+                                          PRECISIONS[precision]))
+
+
+class Server:
+    """Continuous-batching server (rpchol_server_*): jobs are admitted by
+    device memory and slots as they free up and overlap on the GPU."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int):
+        self._s = ctypes.c_void_p()
+        _check(lib().rpchol_server_create(int(mem_budget_bytes), int(max_slots),
+                                          ctypes.byref(self._s)), "rpchol_server_create")
+
+    def submit(self, X, kernel: str, sigma: float, k: int, T: int = 0, seed: int = 0,
+               precision: str = "mixed") -> int:
+        Xn = np.ascontiguousarray(X)
+        if Xn.dtype not in (np.float32, np.float64):
+            Xn = Xn.astype(np.float32)
+        job = Job(KERNELS[kernel], float(sigma), Xn.ctypes.data, Xn.shape[0], Xn.shape[1],
+                  0 if Xn.dtype == np.float32 else 1, int(k), int(T), PRECISIONS[precision],
+                  int(seed) & (2**64 - 1))
+        t = ctypes.c_uint64()
+        _check(lib().rpchol_server_submit(self._s, ctypes.byref(job), ctypes.byref(t)),
+               "rpchol_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_ms: int = 0) -> dict:
+        r = JobResult()
+        _check(lib().rpchol_server_poll(self._s, int(ticket), int(wait_ms), ctypes.byref(r)),
+               "rpchol_server_poll")
+        out = {k: getattr(r, k) for k, _ in JobResult._fields_}
+        out["state"] = JOB_STATES[r.state]
+        return out
+
+    def copy_factor(self, ticket: int, N: int, rank: int, dtype=np.float32):
+        F = np.zeros((N, max(rank, 1)), dtype=dtype)
+        P = np.zeros(max(rank, 1), dtype=np.int64)
+        _check(lib().rpchol_server_copy_factor(self._s, int(ticket), F.ctypes.data,
+                                               max(rank, 1), P.ctypes.data),
+               "rpchol_server_copy_factor")
+        return F[:, :rank], P[:rank]
+
+    def release(self, ticket: int):
+        _check(lib().rpchol_server_release(self._s, int(ticket)), "rpchol_server_release")
+
+    def close(self):
+        if getattr(self, "_s", None) and self._s.value:
+            lib().rpchol_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:

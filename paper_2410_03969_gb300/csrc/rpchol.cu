@@ -746,6 +746,31 @@ rpchol_status batch_record(rpchol_batch* b) {
 
 extern "C" {
 
+int64_t rpchol_context_bytes(int64_t N, int32_t d, int64_t k_max, int32_t T_max,
+                             int32_t precision) {
+  if (N < 1 || d < 1 || k_max < 1 || T_max < 1) return 0;
+  const bool mixed = precision == RPCHOL_MIXED;
+  const long long xld = round_up(d, kLdAlign), ldF = round_up(k_max, kLdAlign);
+  const long long ntiles = (N + kTileRows - 1) / kTileRows;
+  const long long bf = mixed ? 4 : 8;
+  long long b = 0;
+  b += 4 * N * xld + 4 * N;                           // X, norms
+  b += 8 * N + 8 * ntiles;                            // d, tile sums
+  b += 8 * (ntiles * 8 <= 160 * 1024 ? ntiles : ntiles * (kTMax / 8));  // tile prefix
+  b += bf * N * ldF;                                  // F
+  b += 8 * k_max + 4 * kTMax + 16 * kTMax + 4 * kTMax;  // pivots, proposals, uniforms
+  b += 8 * 2LL * kTMax * kTMax + 8 * 2LL * kTMax * T_max;  // H, Lw, L, Linv
+  b += 8LL * kHTilesMax * kHSplitMax * 256 + 4 * kHTilesMax;  // H partials, counters
+  b += 8 * (2 + 2048 + 2) + (long long)sizeof(DevState);
+  b += 8LL * T_max * (ldF + kTMax);                   // extended operand rows
+  if (mixed && N >= 128) {
+    b += 2 * 4 * N * xld;                             // TF32 planes of X
+    b += 2 * 4LL * kTMax * ldF + 2 * 4LL * kTMax * xld;  // planes of F(S,:), X_S
+    b += 4LL * kTMax + 4LL * kTMax * kTMax + 4LL * kTMax;
+  }
+  return (int64_t)b;
+}
+
 rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int32_t* T,
                                   rpchol_batch** out) {
   g_err[0] = 0;
