@@ -38,6 +38,14 @@ METRIC = "time-to-rank-k & pivots/s vs plain RPCholesky, 1 GB300, equal trace er
 UNIT = "pivots/s"
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line is the only stdout)."""
+    print("[bench %7.1fs] %s" % (time.perf_counter() - _T0, msg), file=sys.stderr, flush=True)
+
+
 def _pct(v, q):
     v = sorted(v)
     if not v:
@@ -124,6 +132,114 @@ def job_throughput(local_ms, steps, k, world, device):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     return total_ms, world * steps * k / (total_ms / 1e3)
+
+
+def batched_measure(args):
+    """Batched workload (uneven Matern-5/2 instances, N log-uniform in
+    [2000, 50000], d in {8, 16, 32}, k uniform in [100, 1000]): T per shape
+    class from the autotuner, then all instances in one batch launch, timed
+    with CUDA events, against the same instances run one after another."""
+    import torch
+    import paper_2410_03969_gb300 as rp
+    from paper_2410_03969_gb300 import autotune
+    probs = workloads.batched_matern(0, count=args.batched)
+    tuner = autotune.Autotuner(precision="mixed", repeats=1)
+    t0 = time.perf_counter()
+    Ts = []
+    for i, p in enumerate(probs):
+        Ts.append(tuner.choose(p.X, p.kernel, p.sigma, p.k))
+        if i % 32 == 31:
+            log("  autotuned %d/%d instances (%d classes)" % (i + 1, len(probs), len(tuner.cache)))
+    tune_s = time.perf_counter() - t0
+    fs = [rp.Factorizer(p.X, p.kernel, p.sigma, k_max=p.k, T_max=T, precision="mixed",
+                        instance=i) for i, (p, T) in enumerate(zip(probs, Ts))]
+    ks = [p.k for p in probs]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def one_by_one(seed):
+        for i, (f, T) in enumerate(zip(fs, Ts)):
+            f.run(ks[i], T, seed + i)
+
+    log("  %d contexts created" % len(fs))
+    one_by_one(7)  # record each context's graph
+    log("  one by one done")
+    seq_ms = min(timed(lambda: one_by_one(100 + 1000 * r)) for r in range(2))
+    with rp.Batch(fs, Ts) as b:
+        log("  batch recorded")
+        b.run(ks, [7 + i for i in range(len(fs))])
+        bat_ms = min(timed(lambda: b.run(ks, [200 + 1000 * r + i for i in range(len(fs))]))
+                     for r in range(3))
+        terr = [f.stats()["trace_error"] for f in fs[:16]]
+    for f in fs:
+        f.close()
+    piv = sum(ks)
+    classes = {}
+    for p, T in zip(probs, Ts):
+        classes[autotune.shape_class(p.N, p.d, p.k, p.kernel)] = T
+    return {"instances": len(probs), "pivots": piv, "batch_ms": bat_ms,
+            "pivots_per_s": piv / (bat_ms / 1e3), "one_by_one_ms": seq_ms,
+            "speedup_vs_one_by_one": seq_ms / bat_ms, "autotune_s": tune_s,
+            "shape_classes": len(classes), "T_chosen": sorted(set(Ts)),
+            "trace_error_mean_first16": statistics.mean(terr),
+            "launch": "one CUDA graph, one conditional round loop per instance"}
+
+
+def serving_measure(args):
+    """Serving workload: Poisson arrivals (20 jobs/s) of jobs with N
+    log-uniform in [1e3, 2e5], d = 32 mixture points, Gaussian or l2-Laplace,
+    k uniform in [200, 2000], FP32 factors admitted by memory; p50/p99 of the
+    end-to-end latency (arrival -> factor ready on the device) and the
+    throughput, for the stream as it arrives and for the same jobs in one
+    burst."""
+    import paper_2410_03969_gb300 as rp
+    jobs = workloads.serving_stream(0, jobs=args.serving)
+    budget, slots = 64 << 30, 16
+
+    def drive(arrivals):
+        import queue
+        with rp.Server(budget, slots) as srv:
+            t0 = time.perf_counter()
+            pending, res = queue.Queue(), []
+
+            def collect():  # oldest first: it is admitted before any later job
+                for _ in range(len(arrivals)):
+                    t = pending.get()
+                    res.append(srv.poll(t, wait_ms=-1))
+                    srv.release(t)  # the client has its result; free the memory
+
+            th = threading.Thread(target=collect)
+            th.start()
+            for i, (t_arr, j) in enumerate(zip(arrivals, jobs)):
+                dt = t_arr - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                p = j.problem
+                pending.put(srv.submit(p.X, p.kernel, p.sigma, p.k, seed=i))
+            th.join()
+            wall = time.perf_counter() - t0
+        lat = [r["latency_ms"] for r in res]
+        ok = sum(1 for r in res if r["state"] == "finished")
+        return {"jobs": len(res), "finished": ok, "p50_ms": _pct(lat, 50),
+                "p99_ms": _pct(lat, 99), "mean_queue_ms": statistics.mean(r["queue_ms"] for r in res),
+                "wall_s": wall, "jobs_per_s": len(res) / wall,
+                "pivots_per_s": sum(r["rank"] for r in res) / wall,
+                "trace_error_mean": statistics.mean(r["trace_error"] for r in res)}
+
+    log("  %d jobs generated" % len(jobs))
+    stream = drive([j.arrival_s for j in jobs])
+    log("  stream done")
+    burst = drive([0.0] * len(jobs))
+    return {"arrival": "Poisson 20 jobs/s", "budget_bytes": budget, "slots": slots,
+            "stream": stream, "burst": burst}
 
 
 def _problem(args):
@@ -228,6 +344,7 @@ def ours_arm(args):
         f.run(k, T, seed_base + 900 + i)
     torch.cuda.synchronize()
 
+    log("timed region")
     # ---- timed region: K factorisations, per-step CUDA events, L2 flushed between steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -262,6 +379,7 @@ def ours_arm(args):
 
     extra = {}
     if rank == 0 and not args.quick:
+        log("simple RPCholesky on the same GPU")
         # ---- simple RPCholesky on the same GPU, same precision (the baseline)
         pm, pterr = [], []
         for i in range(args.plain_steps):
@@ -279,6 +397,7 @@ def ours_arm(args):
         extra["speedup_vs_plain_gpu"] = statistics.median(pm) / statistics.median(step_ms)
         extra["trace_error_ratio_vs_plain_gpu"] = (sum(terr) / len(terr)) / (
             sum(pterr) / len(pterr))
+        log("other precision mode")
         # ---- other precision mode, for context
         other = "fp64" if prec == "mixed" else None
         if other:
@@ -297,6 +416,7 @@ def ours_arm(args):
                     ot.append(g.stats()["trace_error"])
             extra["fp64_mode"] = {"ms_p50": _pct(om, 50), "trace_error_mean": sum(ot) / len(ot)}
 
+        log("roofline of the dominant kernel")
         # ---- roofline of the dominant kernel: profiled pass (per-kernel events)
         peaks, src = _peaks()
         with rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=k, T_max=T, precision=prec,
@@ -326,6 +446,7 @@ def ours_arm(args):
                      "phase_ms": sp["phase_ms"]})
         extra["roofline"] = roof
 
+        log("end to end through the public API with host buffers")
         # ---- end to end through the public API with host buffers
         Xh = torch.from_numpy(prob.X).pin_memory()
         es = 4 if prec == "mixed" else 8
@@ -348,7 +469,14 @@ def ours_arm(args):
                         "path": "rpchol_create from pinned host X, rpchol_run, "
                                 "rpchol_copy_factor_raw to pinned host F and pivots, destroy"}
         if not args.no_cpu_baseline:
+            log("cpu baseline (oracle)")
             extra["cpu_baseline"] = oracle_sample(prob, budget_s=args.cpu_budget)
+        if args.batched:
+            log("batched workload")
+            extra["batched"] = batched_measure(args)
+        if args.serving:
+            log("serving workload")
+            extra["serving"] = serving_measure(args)
     f.close()
 
     if rank == 0:
@@ -393,6 +521,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=256,
+                    help="instances of the batched workload to time (0 = skip)")
+    ap.add_argument("--serving", type=int, default=40,
+                    help="jobs of the serving workload to time (0 = skip)")
     ap.add_argument("--quick", action="store_true", help="timed region only")
     ap.add_argument("--n-points", type=int, default=0,
                     help="override N of the workload (small profiling cases; not a bench line)")

@@ -133,3 +133,19 @@ def test_mixed_plain_baseline(rp):
     o = oracle.rpc_plain(prob.k, 3, X=prob.X, kernel=prob.kernel, sigma=prob.sigma)
     # the first pivots coincide before FP32 rounding can matter
     assert g["S"][0] == o["S"][0]
+
+
+@pytest.mark.parametrize("T", [160, 256])
+def test_large_blocks_over_many_tiles(rp, T):
+    """Block sizes above 128 hold one tile's accumulators in all of TMEM;
+    with several 128-row tiles per CTA the tiles then alternate with their
+    epilogues.  Several rounds on 40,000 points exercise that hand-off."""
+    X = workloads.gaussian_mixture(40000, 16, 5)
+    sigma = workloads.median_pairs_bandwidth(X, 5, 1000)
+    with rp.Factorizer(X, "gaussian", sigma, k_max=700, T_max=T, precision="mixed") as f:
+        f.run(700, T, 3).sync()
+        st = f.stats()
+        g = f.copy_factor(F=False)
+    assert st["status"] == 0 and st["rank"] == 700 and st["rounds"] >= 3
+    assert 0.0 < st["trace_error"] < 0.2
+    assert np.all(g["d"] >= 0.0)
