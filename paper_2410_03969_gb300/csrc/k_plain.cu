@@ -25,7 +25,10 @@ struct Acc<float> {
   using T = float;
 };
 
-// One warp per row: g_r = kappa(x_r, x_s) - F(r, 0:i) . F(s, 0:i).
+// One warp per row: g_r = kappa(x_r, x_s) - F(r, 0:i) . F(s, 0:i).  In mixed
+// mode (FP32 factor) the row of F streams as float4 and the distance and the
+// kernel map are FP32, as in the accelerated column step (FP64 is slow on
+// this GPU); FP64 mode keeps every step in FP64.
 template <typename TF>
 __global__ void __launch_bounds__(256) k_plain_col(DevState* st, const float* __restrict__ X,
                                                    int xld, int d, int kind, double inv_sigma,
@@ -41,24 +44,39 @@ __global__ void __launch_bounds__(256) k_plain_col(DevState* st, const float* __
   const TF* fr = F + r * ldF;
   const TF* fs = F + (long long)s * ldF;
   A acc = 0;
-  for (long long m = lane; m < i; m += 32) acc += (A)fr[m] * (A)fs[m];
+  long long m0 = 0;
+  if constexpr (sizeof(TF) == 4) {
+    // rows start on 128-byte boundaries (ldF is a multiple of 32)
+    const float4* fr4 = (const float4*)fr;
+    const float4* fs4 = (const float4*)fs;
+    const long long i4 = i >> 2;
+    for (long long m = lane; m < i4; m += 32) {
+      const float4 a = fr4[m], b = fs4[m];
+      acc = fmaf(a.x, b.x, acc);
+      acc = fmaf(a.y, b.y, acc);
+      acc = fmaf(a.z, b.z, acc);
+      acc = fmaf(a.w, b.w, acc);
+    }
+    m0 = i4 << 2;
+  }
+  for (long long m = m0 + lane; m < i; m += 32) acc += (A)fr[m] * (A)fs[m];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  double r2 = 0.0;
+  A r2 = 0;
   if (r != s) {
     const float* xa = X + r * xld;
     const float* xb = X + (long long)s * xld;
     for (int l = lane; l < d; l += 32) {
-      const double t = (double)xa[l] - (double)xb[l];
+      const A t = (A)xa[l] - (A)xb[l];
       r2 += t * t;
     }
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
   }
   if (lane == 0) {
-    double kv = 1.0;
-    if (r != s) kv = phi_r2<double>(kind, inv_sigma, r2);
-    const double g = kv - (double)acc;
+    A kv = 1;
+    if (r != s) kv = phi_r2<A>(kind, (A)inv_sigma, r2);
+    const A g = kv - acc;
     F[r * ldF + i] = (TF)g;
-    if (r == s) st->gs = g;
+    if (r == s) st->gs = (double)g;
   }
 }
 

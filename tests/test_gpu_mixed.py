@@ -149,3 +149,26 @@ def test_large_blocks_over_many_tiles(rp, T):
     assert st["status"] == 0 and st["rank"] == 700 and st["rounds"] >= 3
     assert 0.0 < st["trace_error"] < 0.2
     assert np.all(g["d"] >= 0.0)
+
+
+def test_many_chunks_per_tile_match_the_exact_factor_of_the_pivots(rp):
+    """40,000 points, small blocks (s <= 48, so the operand ring runs at its
+    deepest) and several tiles per CTA: the factor must equal the exact
+    Nystrom factor of the GPU's own pivots (oracle, FP64) to FP32 accuracy
+    for every seed, which fails if any operand slot is reused too early."""
+    X = workloads.gaussian_mixture(40000, 12, 9)
+    sigma = workloads.median_pairs_bandwidth(X, 9, 1000)
+    with rp.Factorizer(X, "gaussian", sigma, k_max=400, T_max=48, precision="mixed") as f:
+        for seed in range(3):
+            f.run(400, 48, 50 + seed).sync()
+            g = f.copy_factor()
+            st = f.stats()
+            assert st["status"] == 0 and g["rank"] == 400
+            # the same run again is bit-identical (a slot reused too early
+            # shows up as run-to-run differences first)
+            f.run(400, 48, 50 + seed).sync()
+            assert np.array_equal(f.copy_factor()["F"], g["F"]), seed
+            Fx, dx, tex = oracle.fixed_pivot_factor(g["S"], X=X, kernel="gaussian", sigma=sigma)
+            err = np.linalg.norm(g["F"] - Fx) / np.linalg.norm(Fx)
+            assert err <= 5e-4, (seed, err)
+            assert st["trace_error"] == pytest.approx(tex / 40000, rel=5e-3)
