@@ -221,6 +221,135 @@ __device__ __forceinline__ void epi_row_tmem(const EpiRow& e, int nblk, float& r
     tc::tmem_st16_sync(e.d1 + 16 * bi, acc);  // G_b over the consumed D1 block
   }
 }
+// ---- quad layout: thread t of a warp holds 4 rows x 4 columns of each
+// 16-column block (tmem_ld_quad16), so that the W rows it needs differ
+// between the 4 threads of a quad instead of being one broadcast value.
+struct EpiQuad {
+  uint32_t d1, d2;       // TMEM D1 / D2 of the warp's lane quarter (column 0)
+  const float* W;        // W blocks of the round
+  const float* nrmSs;    // squared norms of the round's pivots
+  const double* L;       // FP64 Cholesky factor of the round
+  float* frow[4];        // F(row ri, rank), nullptr beyond N
+  float nr[4];           // squared norms of the rows
+  int jpiv[4];           // index among the round's pivots, or -1
+  int s, nF, kind, ldL, cq, lane, even;
+  float inv_sigma;
+};
+
+// acc[ri] (columns 2cq..2cq+1 and 8+2cq..9+2cq) += sum over the 16 columns
+// kappa of block X (held across the quad) of X[ri][kappa] W(kappa, col)
+__device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float (&X)[4][4],
+                                               const float* Wblk, int lane, int cq) {
+  const int qbase = lane & ~3;
+#pragma unroll
+  for (int kp = 0; kp < 16; ++kp) {
+    const int src = qbase | ((kp & 7) >> 1);
+    const int cj = 2 * (kp >> 3) + (kp & 1);
+    const float2 w01 = *(const float2*)(Wblk + 16 * kp + 2 * cq);
+    const float2 w89 = *(const float2*)(Wblk + 16 * kp + 8 + 2 * cq);
+#pragma unroll
+    for (int ri = 0; ri < 4; ++ri) {
+      const float xv = __shfl_sync(0xffffffffu, X[ri][cj], src);
+      const float2 x2 = make_float2(xv, xv);
+      acc[ri][0] = __ffma2_rn(x2, w01, acc[ri][0]);
+      acc[ri][1] = __ffma2_rn(x2, w89, acc[ri][1]);
+    }
+  }
+}
+
+// G L^* = R by blocks of 16 columns in the quad layout; finished blocks of G
+// go back into TMEM over the consumed D1 blocks.  Returns each row's
+// Kahan-compensated partial sum of squares (this thread's 4 columns of
+// every block) in rsq / rc.
+__device__ __forceinline__ void epi_tile_quad(const EpiQuad& e, int nblk, float (&rsq)[4],
+                                              float (&rc)[4]) {
+  const int cq = e.cq;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int j0 = 16 * bi;
+    const float* Wb = e.W + 128 * bi * (bi + 1);
+    float2 acc[4][2];
+#pragma unroll
+    for (int ri = 0; ri < 4; ++ri) acc[ri][0] = acc[ri][1] = make_float2(0.f, 0.f);
+    for (int lb = 0; lb < bi; ++lb) {
+      float X[4][4];
+      tc::tmem_ld_quad16(e.d1 + 16 * lb, X);
+      quad_fma_block(acc, X, Wb + 256 * lb, e.lane, cq);
+    }
+    // this block of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2
+    float R[4][4];
+    {
+      float D1v[4][4], D2v[4][4];
+      tc::tmem_ld_quad16(e.d1 + j0, D1v);
+      if (e.nF > 0) {
+        tc::tmem_ld_quad16(e.d2 + j0, D2v);
+      } else {
+#pragma unroll
+        for (int ri = 0; ri < 4; ++ri)
+#pragma unroll
+          for (int cj = 0; cj < 4; ++cj) D2v[ri][cj] = 0.f;
+      }
+#pragma unroll
+      for (int cj = 0; cj < 4; ++cj) {
+        const int col = j0 + 8 * (cj >> 1) + 2 * cq + (cj & 1);
+        const float ns = e.nrmSs[col];
+#pragma unroll
+        for (int ri = 0; ri < 4; ++ri) {
+          const float kv = col == e.jpiv[ri]
+                               ? 1.f
+                               : phi_r2<float>(e.kind, e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
+          R[ri][cj] = col < e.s ? kv - D2v[ri][cj] : 0.f;
+        }
+      }
+    }
+    quad_fma_block(acc, R, Wb + 256 * bi, e.lane, cq);
+    float G[4][4];
+#pragma unroll
+    for (int ri = 0; ri < 4; ++ri) {
+      G[ri][0] = acc[ri][0].x;
+      G[ri][1] = acc[ri][0].y;
+      G[ri][2] = acc[ri][1].x;
+      G[ri][3] = acc[ri][1].y;
+      if (e.jpiv[ri] >= 0) {
+        // A pivot row of this round: in exact arithmetic R(S,:) = L L^*, so
+        // G(S_j,:) = L(j,:) and its residual is zero.  The exact values (L
+        // from the FP64 Cholesky of H) replace the rounded contraction, so a
+        // chosen pivot keeps zero proposal weight and its row of F agrees
+        // with the H that later rounds form from it.
+#pragma unroll
+        for (int cj = 0; cj < 4; ++cj) {
+          const int col = j0 + 8 * (cj >> 1) + 2 * cq + (cj & 1);
+          G[ri][cj] = (col < e.s && col <= e.jpiv[ri])
+                          ? (float)e.L[(long long)e.jpiv[ri] * e.ldL + col]
+                          : 0.f;
+        }
+      }
+    }
+    tc::tmem_st_quad16(e.d1 + j0, G);  // G_b over the consumed D1 block
+#pragma unroll
+    for (int ri = 0; ri < 4; ++ri) {
+      if (e.frow[ri]) {
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int col = j0 + 8 * g + 2 * cq;
+          float* dst = e.frow[ri] + col;
+          if (e.even && col + 1 < e.s) {
+            *(float2*)dst = make_float2(G[ri][2 * g], G[ri][2 * g + 1]);
+          } else {
+            if (col < e.s) dst[0] = G[ri][2 * g];
+            if (col + 1 < e.s) dst[1] = G[ri][2 * g + 1];
+          }
+        }
+      }
+      float bs = 0.f;
+#pragma unroll
+      for (int cj = 0; cj < 4; ++cj) bs = fmaf(G[ri][cj], G[ri][cj], bs);
+      const float y = bs - rc[ri];
+      const float t = rsq[ri] + y;
+      rc[ri] = (t - rsq[ri]) - y;
+      rsq[ri] = t;
+    }
+  }
+}
 }  // namespace
 
 struct TcArgs {
@@ -455,15 +584,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const long long tile = blockIdx.x + (long long)it * gridDim.x;
       if (tile >= ntiles) break;
       const long long row0 = tile * kBM;
-      const long long grow = row0 + row;
+      // this thread's rows: ri -> 32 q + lane / 4 + 16 (ri >> 1) + 8 (ri & 1)
+      const int cq = lane & 3;
+      long long growv[4];
+      EpiQuad eq;
+#pragma unroll
+      for (int ri = 0; ri < 4; ++ri) {
+        growv[ri] = row0 + 32 * q + (lane >> 2) + 16 * (ri >> 1) + 8 * (ri & 1);
+        const bool lv = growv[ri] < a.N;
+        eq.frow[ri] = lv ? a.F + growv[ri] * a.ldF + rank : nullptr;
+        eq.nr[ri] = lv ? a.nrm[growv[ri]] : 0.f;  // loaded while the accumulators fill
+        eq.jpiv[ri] = -1;
+      }
+      // this thread updates d for row ri = cq (each row once across its quad)
+      const long long grow = growv[cq];
       const bool live = grow < a.N;
-      // the row's norm and residual diagonal, and whether it is a pivot row,
-      // while the accumulators fill
-      const float nr = live ? a.nrm[grow] : 0.f;
       const double dold = live ? a.dvec[grow] : 0.0;
-      int jpiv = -1;
-      for (int j = 0; j < s; ++j)
-        if ((long long)Ss[j] == grow) jpiv = j;
+      for (int j = 0; j < s; ++j) {
+        const long long p = (long long)Ss[j];
+#pragma unroll
+        for (int ri = 0; ri < 4; ++ri)
+          if (p == growv[ri]) eq.jpiv[ri] = j;
+      }
       tc::mbar_wait_warp(&accf[grp], (uint32_t)((it >> 1) & 1), tc::globaltimer_ns() + kWaitNs,
                          abort_flag);
       // one thread's reading of the abort flag decides for the whole group
@@ -475,32 +617,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc::tc_fence_after();
-      const uint32_t d1 = tbase + lane_off + (uint32_t)((nbuf == 2 ? grp : 0) * 256);
-      const uint32_t d2 = d1 + (nbuf == 2 ? 128u : 256u);
-      EpiRow er;
-      er.d1 = d1;
-      er.d2 = d2;
-      er.W = Lo.w_resident ? Wsm : a.W;
-      er.nrmSs = nrmSs;
-      er.L = a.L;
-      er.frow = live ? a.F + grow * a.ldF + rank : nullptr;
-      er.s = s;
-      er.nF = nF;
-      er.jpiv = jpiv;
-      er.mis = mis;
-      er.kind = a.kind;
-      er.ldL = a.ldL;
-      er.nr = nr;
-      er.inv_sigma = a.inv_sigma;
-      float rsq = 0.f, rc = 0.f;  // Kahan-compensated sum of G^2 over the row
-      epi_row_tmem(er, nblk, rsq, rc);
+      eq.d1 = tbase + lane_off + (uint32_t)((nbuf == 2 ? grp : 0) * 256);
+      eq.d2 = eq.d1 + (nbuf == 2 ? 128u : 256u);
+      eq.W = Lo.w_resident ? Wsm : a.W;
+      eq.nrmSs = nrmSs;
+      eq.L = a.L;
+      eq.s = s;
+      eq.nF = nF;
+      eq.kind = a.kind;
+      eq.ldL = a.ldL;
+      eq.cq = cq;
+      eq.lane = lane;
+      eq.even = (rank & 1) == 0;
+      eq.inv_sigma = a.inv_sigma;
+      float rsq[4] = {0.f, 0.f, 0.f, 0.f}, rc[4] = {0.f, 0.f, 0.f, 0.f};
+      epi_tile_quad(eq, nblk, rsq, rc);
       tc::tc_fence_before();
       tc::mbar_arrive_warp(&tfree[nbuf == 2 ? grp : 0]);  // TMEM buffer free for tile it + nbuf
-      // ---- residual diagonal (FP64) and the tile's sum of d
+      // ---- row sums of G^2 across the quad (FP64), residual diagonal, tile sum
+      double sq[4];
+#pragma unroll
+      for (int ri = 0; ri < 4; ++ri) {
+        sq[ri] = (double)rsq[ri] - (double)rc[ri];
+        sq[ri] += __shfl_xor_sync(0xffffffffu, sq[ri], 1);
+        sq[ri] += __shfl_xor_sync(0xffffffffu, sq[ri], 2);
+      }
+      const double mysq = cq == 0 ? sq[0] : cq == 1 ? sq[1] : cq == 2 ? sq[2] : sq[3];
+      const int myjp = cq == 0 ? eq.jpiv[0] : cq == 1 ? eq.jpiv[1] : cq == 2 ? eq.jpiv[2] : eq.jpiv[3];
       double dn = 0.0;
       if (live) {
-        const double v = dold - ((double)rsq - (double)rc);
-        dn = (v > 0.0 && jpiv < 0) ? v : 0.0;
+        const double v = dold - mysq;
+        dn = (v > 0.0 && myjp < 0) ? v : 0.0;
         a.dvec[grow] = dn;
       }
       for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);

@@ -372,10 +372,11 @@ __device__ __forceinline__ int own_off(int j) {
 // are done on the bit patterns (exponent rebased by 1023 - 127; y0 / 2 is
 // exact), so that only the three operations of the step use the FP64 pipe.
 // FP64 mode takes a second step (about 1 ulp).  Arguments outside
-// [1e-30, 1e30] take sqrt and divide.
+// [1e-30, 1e30] (checked on the bit pattern) take sqrt and divide.
 __device__ __forceinline__ double rsqrt_newton(double x, bool second) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
   const long long xb = __double_as_longlong(x);
+  // 1e-30 < x < 1e30 on the bit pattern (positive doubles order like integers)
+  if (!(xb > 0x39b4484bfeebc2a0ll && xb < 0x46293e5939a08ceall)) return 1.0 / sqrt(x);
   const float xf = __int_as_float((int)((xb >> 29) - (896ll << 23)));
   const float rf = rsqrtf(xf);
   const double y = __longlong_as_double(((long long)__float_as_int(rf) + (896ll << 23)) << 29);

@@ -258,6 +258,59 @@ __device__ __forceinline__ void tmem_st16_sync(uint32_t taddr, const float* v) {
       : "memory");
 }
 
+// 16x256b accesses: in a 16-lane half of the warp's lane quarter, thread t
+// holds lanes t/4 and t/4 + 8, columns 2(t%4) and 2(t%4) + 1 of an 8-column
+// group.  The quad form below covers a warp's 32 lanes and 16 columns
+// (halves h = 0, 1 at lane offsets 0 and 16; groups g = 0, 1 at column
+// offsets 0 and 8): thread t gets rows r = t/4 + {0, 8, 16, 24} and columns
+// 2(t%4) + {0, 1, 8, 9}, as v[ri][cj] with ri = 2h + i (row offset 16h + 8i)
+// and cj = 2g + e (column offset 8g + e).  One wait covers the four loads.
+__device__ __forceinline__ void tmem_ld_quad16(uint32_t ta, float (&v)[4][4]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0, %1, %2, %3}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4, %5, %6, %7}, [%17];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%8, %9, %10, %11}, [%18];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%12, %13, %14, %15}, [%19];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(ta + 8u), "r"(ta + (16u << 16)), "r"(ta + (16u << 16) + 8u)
+      : "memory");
+  // load k = 2h + g holds (i, e) = (0,0), (0,1), (1,0), (1,1)
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) v[2 * h + i][2 * g + e] = __uint_as_float(r[4 * (2 * h + g) + 2 * i + e]);
+}
+
+__device__ __forceinline__ void tmem_st_quad16(uint32_t ta, const float (&v)[4][4]) {
+  uint32_t r[16];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) r[4 * (2 * h + g) + 2 * i + e] = __float_as_uint(v[2 * h + i][2 * g + e]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%0], {%4, %5, %6, %7};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%1], {%8, %9, %10, %11};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%2], {%12, %13, %14, %15};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%3], {%16, %17, %18, %19};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+      "r"(ta + 8u), "r"(ta + (16u << 16)), "r"(ta + (16u << 16) + 8u), "r"(r[0]), "r"(r[1]),
+      "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
 // TF32 head of an fp32 value: x rounded to nearest (ties away) at 10
 // explicit mantissa bits, low 13 bits zero, so that the tensor core sees it
 // exactly whether it truncates or rounds its inputs; the tail x - head is
