@@ -257,11 +257,27 @@ __device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float 
   }
 }
 
+template <int KIND>
+__device__ __forceinline__ void r_quad(const EpiQuad& e, int j0, const float (&D1v)[4][4],
+                                       const float (&D2v)[4][4], float (&R)[4][4]) {
+#pragma unroll
+  for (int cj = 0; cj < 4; ++cj) {
+    const int col = j0 + 8 * (cj >> 1) + 2 * e.cq + (cj & 1);
+    const float ns = e.nrmSs[col];
+#pragma unroll
+    for (int ri = 0; ri < 4; ++ri) {
+      const float kv =
+          col == e.jpiv[ri] ? 1.f : phi_r2<float>(KIND, e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
+      R[ri][cj] = col < e.s ? kv - D2v[ri][cj] : 0.f;
+    }
+  }
+}
+
 // G L^* = R by blocks of 16 columns in the quad layout; finished blocks of G
 // go back into TMEM over the consumed D1 blocks.  Returns each row's
 // Kahan-compensated partial sum of squares (this thread's 4 columns of
 // every block) in rsq / rc.
-__device__ __forceinline__ void epi_tile_quad(const EpiQuad& e, int nblk, float (&rsq)[4],
+__device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (&rsq)[4],
                                               float (&rc)[4]) {
   const int cq = e.cq;
   for (int bi = 0; bi < nblk; ++bi) {
@@ -288,17 +304,12 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad& e, int nblk, float 
 #pragma unroll
           for (int cj = 0; cj < 4; ++cj) D2v[ri][cj] = 0.f;
       }
-#pragma unroll
-      for (int cj = 0; cj < 4; ++cj) {
-        const int col = j0 + 8 * (cj >> 1) + 2 * cq + (cj & 1);
-        const float ns = e.nrmSs[col];
-#pragma unroll
-        for (int ri = 0; ri < 4; ++ri) {
-          const float kv = col == e.jpiv[ri]
-                               ? 1.f
-                               : phi_r2<float>(e.kind, e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
-          R[ri][cj] = col < e.s ? kv - D2v[ri][cj] : 0.f;
-        }
+      // the kernel map, with the kind resolved outside the loop so that the
+      // 16 evaluations interleave
+      switch (e.kind) {
+        case 0: r_quad<0>(e, j0, D1v, D2v, R); break;
+        case 1: r_quad<1>(e, j0, D1v, D2v, R); break;
+        default: r_quad<2>(e, j0, D1v, D2v, R); break;
       }
     }
     quad_fma_block(acc, R, Wb + 256 * bi, e.lane, cq);
@@ -597,7 +608,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         eq.jpiv[ri] = -1;
       }
       // this thread updates d for row ri = cq (each row once across its quad)
-      const long long grow = growv[cq];
+      const long long grow = row0 + 32 * q + (lane >> 2) + 16 * (cq >> 1) + 8 * (cq & 1);
       const bool live = grow < a.N;
       const double dold = live ? a.dvec[grow] : 0.0;
       for (int j = 0; j < s; ++j) {
