@@ -391,12 +391,14 @@ def ours_arm(args):
             torch.cuda.synchronize()
             pm.append(a.elapsed_time(b))
             pterr.append(f.stats()["trace_error"])
+    if rank == 0 and not args.quick and pm:
         extra["plain_gpu"] = {
             "ms_p50": _pct(pm, 50), "pivots_per_s": k / (statistics.median(pm) / 1e3),
             "trace_error_mean": sum(pterr) / len(pterr), "steps": len(pm), "precision": prec}
         extra["speedup_vs_plain_gpu"] = statistics.median(pm) / statistics.median(step_ms)
         extra["trace_error_ratio_vs_plain_gpu"] = (sum(terr) / len(terr)) / (
             sum(pterr) / len(pterr))
+    if rank == 0 and not args.quick:
         log("other precision mode")
         # ---- other precision mode, for context
         other = "fp64" if prec == "mixed" else None

@@ -48,10 +48,14 @@ namespace rpchol {
 namespace {
 constexpr int kTcThreads = 384;
 constexpr int kBM = 128;
-constexpr int kStageA = kBM * 32 * 4;  // 16 KiB
+constexpr int kKc = 32;                  // K extent of a chunk (fp32 elements)
+constexpr int kRowBytes = kKc * 4;       // one 128-byte swizzle row per operand row
+constexpr int kStageA = kBM * kRowBytes;  // 16 KiB
+constexpr int kBoxB = 64 * kRowBytes;     // one 64-row box of a B operand, 8 KiB
 constexpr int kSmemMax = 227 * 1024;
 constexpr int kSmallBytes = 4 * 1024;  // pivots, their norms, barriers, flags, sums
 constexpr int kMaxStages = 4;
+constexpr int kPrefetch = 8;          // A chunks prefetched into L2 ahead of their loads
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct Layout {
@@ -64,7 +68,7 @@ __host__ __device__ inline Layout make_layout(int s) {
   Layout L;
   L.s_pad = (s + 15) & ~15;
   L.nbox = (L.s_pad + 63) >> 6;
-  L.stage_bytes = 2 * kStageA + 2 * L.nbox * 8192;
+  L.stage_bytes = 2 * kStageA + 2 * L.nbox * kBoxB;
   L.nbuf = L.s_pad <= 128 ? 2 : 1;
   const int nblk = L.s_pad >> 4;
   const int wbytes = 512 * nblk * (nblk + 1);
@@ -82,145 +86,6 @@ __host__ __device__ inline Layout make_layout(int s) {
   return L;
 }
 
-// 16 consecutive floats of a row of F, at a position whose alignment class
-// (column index mod 4) is MIS: scalar stores up to the first 16-byte
-// boundary, then float4 stores.
-template <int MIS>
-__device__ __forceinline__ void store16_al(float* dst, const float* v) {
-  constexpr int c0 = (4 - MIS) & 3;
-  constexpr int c1 = c0 + ((16 - c0) & ~3);
-#pragma unroll
-  for (int j = 0; j < c0; ++j) dst[j] = v[j];
-#pragma unroll
-  for (int j = c0; j < c1; j += 4)
-    *(float4*)(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-#pragma unroll
-  for (int j = c1; j < 16; ++j) dst[j] = v[j];
-}
-
-__device__ __forceinline__ void store16(float* dst, const float* v, int ncols, int mis) {
-  if (ncols >= 16) {
-    switch (mis) {
-      case 0: store16_al<0>(dst, v); break;
-      case 1: store16_al<1>(dst, v); break;
-      case 2: store16_al<2>(dst, v); break;
-      default: store16_al<3>(dst, v); break;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < ncols) dst[j] = v[j];
-  }
-}
-
-// acc[jj] += sum_m x[m] W(m, jj), W rows of 16 floats; the 16 sums are
-// kept as 8 pairs and updated with the packed two-lane FP32 FMA.
-template <int M>
-__device__ __forceinline__ void fma_rows(float2* acc, const float* x, const float* W) {
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    const float2 xv = make_float2(x[m], x[m]);
-    const float4* wr = (const float4*)(W + 16 * m);
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const float4 w = wr[g];
-      acc[2 * g] = __ffma2_rn(xv, make_float2(w.x, w.y), acc[2 * g]);
-      acc[2 * g + 1] = __ffma2_rn(xv, make_float2(w.z, w.w), acc[2 * g + 1]);
-    }
-  }
-}
-// One tile row's share of the epilogue: what the block loop needs.
-struct EpiRow {
-  uint32_t d1, d2;      // TMEM addresses of this row's D1 and D2 (column 0)
-  const float* W;       // W blocks of the round (shared or global memory)
-  const float* nrmSs;   // squared norms of the round's pivots
-  const double* L;      // FP64 Cholesky factor of the round, row jpiv
-  float* frow;          // F(row, rank), nullptr beyond N
-  int s, nF, jpiv, mis, kind, ldL;
-  float nr, inv_sigma;
-};
-
-// Block bi of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2, from TMEM.
-__device__ __forceinline__ void r_block(const EpiRow& e, int bi, float* v1) {
-  const int j0 = 16 * bi;
-  float v2[16];
-  if (e.nF > 0) {
-    tc::tmem_ld16x2_sync(e.d1 + j0, e.d2 + j0, v1, v2);
-  } else {
-    tc::tmem_ld16_sync(e.d1 + j0, v1);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) v2[m] = 0.f;
-  }
-#pragma unroll
-  for (int m = 0; m < 16; ++m) {
-    const int c = j0 + m;
-    const float kv =
-        c == e.jpiv ? 1.f : phi_r2<float>(e.kind, e.inv_sigma, e.nr + e.nrmSs[c] - 2.f * v1[m]);
-    v1[m] = c < e.s ? kv - v2[m] : 0.f;
-  }
-}
-
-// Block bi of G is final: pivot-row override, store to F, sum of squares.
-__device__ __forceinline__ void g_block_out(const EpiRow& e, int bi, const float2* acc2,
-                                            float* acc, float& rsq, float& rc) {
-  const int j0 = 16 * bi;
-#pragma unroll
-  for (int jj = 0; jj < 8; ++jj) {
-    acc[2 * jj] = acc2[jj].x;
-    acc[2 * jj + 1] = acc2[jj].y;
-  }
-  if (e.jpiv >= 0) {
-    // A pivot row of this round: in exact arithmetic R(S,:) = L L^*, so
-    // G(S_j,:) = L(j,:) and its residual is zero.  The exact values (L from
-    // the FP64 Cholesky of H) replace the rounded contraction, so a chosen
-    // pivot keeps zero proposal weight and its row of F agrees with the H
-    // that later rounds form from it.
-#pragma unroll
-    for (int jj = 0; jj < 16; ++jj) {
-      const int c = j0 + jj;
-      acc[jj] = (c < e.s && c <= e.jpiv) ? (float)e.L[(long long)e.jpiv * e.ldL + c] : 0.f;
-    }
-  }
-  if (e.frow) store16(e.frow + j0, acc, e.s - j0, e.mis);
-  float bs = 0.f;
-#pragma unroll
-  for (int jj = 0; jj < 16; ++jj) bs = fmaf(acc[jj], acc[jj], bs);
-  const float y = bs - rc;
-  const float t = rsq + y;
-  rc = (t - rsq) - y;
-  rsq = t;
-}
-
-// G L^* = R by blocks of 16 columns,
-//   G_b = sum_{l < j0} G(:, l) W_b(l, :) + sum_m R(:, j0 + m) W_b(j0 + m, :),
-// with the finished blocks of G stored back into TMEM over the consumed D1
-// blocks and read from there.
-__device__ __forceinline__ void epi_row_tmem(const EpiRow& e, int nblk, float& rsq, float& rc) {
-  for (int bi = 0; bi < nblk; ++bi) {
-    const float* Wb = e.W + 128 * bi * (bi + 1);
-    float2 acc2[8];
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) acc2[jj] = make_float2(0.f, 0.f);
-    int lb = 0;
-    for (; lb + 1 < bi; lb += 2) {  // two earlier G blocks per TMEM wait
-      float g0[16], g1[16];
-      tc::tmem_ld16x2_sync(e.d1 + 16 * lb, e.d1 + 16 * lb + 16, g0, g1);
-      fma_rows<16>(acc2, g0, Wb + 256 * lb);
-      fma_rows<16>(acc2, g1, Wb + 256 * (lb + 1));
-    }
-    if (lb < bi) {
-      float g0[16];
-      tc::tmem_ld16_sync(e.d1 + 16 * lb, g0);
-      fma_rows<16>(acc2, g0, Wb + 256 * lb);
-    }
-    float v1[16];
-    r_block(e, bi, v1);
-    fma_rows<16>(acc2, v1, Wb + 256 * bi);
-    float acc[16];
-    g_block_out(e, bi, acc2, acc, rsq, rc);
-    tc::tmem_st16_sync(e.d1 + 16 * bi, acc);  // G_b over the consumed D1 block
-  }
-}
 // ---- quad layout: thread t of a warp holds 4 rows x 4 columns of each
 // 16-column block (tmem_ld_quad16), so that the W rows it needs differ
 // between the 4 threads of a quad instead of being one broadcast value.
@@ -399,8 +264,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const Layout Lo = make_layout(s);
   const int s_pad = Lo.s_pad, nbox = Lo.nbox, SB = Lo.stage_bytes, NS = Lo.stages;
   const int nbuf = Lo.nbuf;
-  const int nX = a.xld >> 5;
-  const int nF = (int)((rank + 31) >> 5);
+  const int nX = a.xld / kKc;
+  const int nF = (int)((rank + kKc - 1) / kKc);
   const int nch = nX + nF;
   const long long ntiles = (a.N + kBM - 1) / kBM;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -408,10 +273,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   unsigned char* small = sm + Lo.small_off;
   int* Ss = (int*)small;                  // [256] pivots of the round (-1 beyond s)
   float* nrmSs = (float*)(small + 1024);  // [256] their squared norms
-  uint64_t* full = (uint64_t*)(small + 2048);  // [kMaxStages]
-  uint64_t* conv = full + kMaxStages;          // [kMaxStages]
+  uint64_t* full = (uint64_t*)(small + 2048);  // [kMaxStages] A operand landed
+  uint64_t* conv = full + kMaxStages;          // [kMaxStages] A split into head and tail
   uint64_t* empty = conv + kMaxStages;         // [kMaxStages]
-  uint64_t* accf = empty + kMaxStages;         // [2] accumulators of a tile complete
+  uint64_t* fullB = empty + kMaxStages;        // [kMaxStages] B operand landed
+  uint64_t* accf = fullB + kMaxStages;         // [2] accumulators of a tile complete
   uint64_t* tfree = accf + 2;                  // [2] epilogue done with a TMEM buffer
   uint32_t* tptr = (uint32_t*)(tfree + 2);
   volatile int* abort_flag = (volatile int*)(tptr + 1);
@@ -432,6 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
       tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&fullB[i], 1);
       tc::mbar_init(&conv[i], 2);   // one arrival per converter warp
       tc::mbar_init(&empty[i], 1);
     }
@@ -455,45 +322,69 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       tc::prefetch_tmap(&tmF);
-      const uint32_t bbytes = (uint32_t)nbox * 8192u;
+      const uint32_t bbytes = (uint32_t)nbox * (uint32_t)kBoxB;
+      // The A operands (rows of F and X, read once per round from HBM) are
+      // pulled into L2 kPrefetch chunks ahead of their shared-memory loads,
+      // so that a stage turns over at L2 rather than HBM latency.
+      long long ptile = blockIdx.x;
+      int pc = 0;
+      auto prefetch_next = [&]() {
+        if (ptile >= ntiles) return;
+        const int prow = (int)(ptile * kBM);
+        if (pc < nX) {
+          tc::tma_prefetch_2d(&tmX, pc * kKc, prow);
+          tc::tma_prefetch_2d(&tmXlo, pc * kKc, prow);
+        } else {
+          tc::tma_prefetch_2d(&tmF, (nF - 1 - (pc - nX)) * kKc, prow);
+        }
+        if (++pc == nch) {
+          pc = 0;
+          ptile += gridDim.x;
+        }
+      };
+      for (int i = 0; i < kPrefetch; ++i) prefetch_next();
       long long g = 0;  // chunks issued so far (all tiles)
       for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         const int row0 = (int)(tile * kBM);
         for (int c = 0; c < nch; ++c, ++g) {
           const int stg = (int)(g % NS);
           if (g >= NS && !tc::mbar_wait_bounded(&empty[stg], (uint32_t)(((g / NS) - 1) & 1),
-                                                tc::globaltimer_ns() + kWaitNs, abort_flag))
+                                                kWaitNs, abort_flag))
             break;
           unsigned char* sA = sm + stg * SB;
           unsigned char* sAlo = sA + kStageA;
           unsigned char* sBh = sA + 2 * kStageA;
-          unsigned char* sBl = sBh + nbox * 8192;
+          unsigned char* sBl = sBh + nbox * kBoxB;
           if (c < nX) {
-            const int x = c * 32;
-            tc::mbar_arrive_expect_tx(&full[stg], 2u * kStageA + 2u * bbytes);
+            const int x = c * kKc;
+            tc::mbar_arrive_expect_tx(&full[stg], 2u * kStageA);
             tc::tma_load_2d(sA, &tmX, x, row0, &full[stg]);
             tc::tma_load_2d(sAlo, &tmXlo, x, row0, &full[stg]);
+            tc::mbar_arrive_expect_tx(&fullB[stg], 2u * bbytes);
             for (int b = 0; b < nbox; ++b) {
-              tc::tma_load_2d(sBh + b * 8192, &tmXSh, x, 64 * b, &full[stg]);
-              tc::tma_load_2d(sBl + b * 8192, &tmXSl, x, 64 * b, &full[stg]);
+              tc::tma_load_2d(sBh + b * kBoxB, &tmXSh, x, 64 * b, &fullB[stg]);
+              tc::tma_load_2d(sBl + b * kBoxB, &tmXSl, x, 64 * b, &fullB[stg]);
             }
           } else {
-            const int x = (nF - 1 - (c - nX)) * 32;  // last F column chunk first
-            tc::mbar_arrive_expect_tx(&full[stg], (uint32_t)kStageA + 2u * bbytes);
+            const int x = (nF - 1 - (c - nX)) * kKc;  // last F column chunk first
+            tc::mbar_arrive_expect_tx(&full[stg], (uint32_t)kStageA);
             tc::tma_load_2d(sA, &tmF, x, row0, &full[stg]);
+            tc::mbar_arrive_expect_tx(&fullB[stg], 2u * bbytes);
             for (int b = 0; b < nbox; ++b) {
-              tc::tma_load_2d(sBh + b * 8192, &tmBh, x, 64 * b, &full[stg]);
-              tc::tma_load_2d(sBl + b * 8192, &tmBl, x, 64 * b, &full[stg]);
+              tc::tma_load_2d(sBh + b * kBoxB, &tmBh, x, 64 * b, &fullB[stg]);
+              tc::tma_load_2d(sBl + b * kBoxB, &tmBl, x, 64 * b, &fullB[stg]);
             }
           }
+          prefetch_next();
         }
       }
       if (*abort_flag) {
         // drain: the (at most NS) issued loads not yet consumed must land
         volatile int dummy = 0;
-        const unsigned long long d2 = tc::globaltimer_ns() + kWaitNs;
-        for (long long q = (g > NS ? g - NS : 0); q < g; ++q)
-          tc::mbar_wait_bounded(&full[q % NS], (uint32_t)((q / NS) & 1), d2, &dummy);
+        for (long long q = (g > NS ? g - NS : 0); q < g; ++q) {
+          tc::mbar_wait_bounded(&full[q % NS], (uint32_t)((q / NS) & 1), kWaitNs, &dummy);
+          tc::mbar_wait_bounded(&fullB[q % NS], (uint32_t)((q / NS) & 1), kWaitNs, &dummy);
+        }
       }
     }
   } else if (warp == 1) {
@@ -506,31 +397,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int buf = it % nbuf;
         if (it >= nbuf &&
             !tc::mbar_wait_bounded(&tfree[buf], (uint32_t)(((it / nbuf) - 1) & 1),
-                                   tc::globaltimer_ns() + kWaitNs, abort_flag))
+                                   kWaitNs, abort_flag))
           break;
         tc::tc_fence_after();
         const uint32_t d1 = tbase + (uint32_t)(buf * 256);           // D1 of this tile
         const uint32_t d2 = d1 + (nbuf == 2 ? 128u : 256u);           // D2 of this tile
         for (int c = 0; c < nch; ++c, ++g) {
           const int stg = (int)(g % NS);
-          if (!tc::mbar_wait_bounded(&conv[stg], (uint32_t)((g / NS) & 1),
-                                     tc::globaltimer_ns() + kWaitNs, abort_flag))
+          // the A split (which waited only for A) and then B
+          if (!tc::mbar_wait_bounded(&conv[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag) ||
+              !tc::mbar_wait_bounded(&fullB[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag))
             break;
           tc::tc_fence_after();
           const uint32_t aA = tc::smem_u32(sm + stg * SB);
           const uint32_t aAlo = aA + kStageA;
           const uint32_t aBh = aA + 2 * kStageA;
-          const uint32_t aBl = aBh + nbox * 8192;
+          const uint32_t aBl = aBh + nbox * kBoxB;
           const uint32_t dt = c < nX ? d1 : d2;
           const bool first = (c == 0) || (c == nX);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
+          for (int kk = 0; kk < kKc / 8; ++kk) {
             const uint64_t da = tc::smem_desc_sw128(aA + 32 * kk);
             const uint64_t dal = tc::smem_desc_sw128(aAlo + 32 * kk);
             const uint64_t dbh = tc::smem_desc_sw128(aBh + 32 * kk);
             const uint64_t dbl = tc::smem_desc_sw128(aBl + 32 * kk);
-            tc::mma_tf32(dt, da, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-            tc::mma_tf32(dt, da, dbl, idesc, 1u);
+            // hi.hi and hi.lo share A: the second takes it from the
+            // collector buffer instead of reading shared memory again
+            tc::mma_tf32_keep_a(dt, da, dbh, idesc, (first && kk == 0) ? 0u : 1u);
+            tc::mma_tf32_reuse_a(dt, da, dbl, idesc, 1u);
             tc::mma_tf32(dt, dal, dbh, idesc, 1u);
           }
           tc::mma_commit(&empty[stg]);
@@ -546,26 +440,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int c = 0; c < nch; ++c, ++g) {
         const int stg = (int)(g % NS);
         if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g / NS) & 1),
-                                tc::globaltimer_ns() + kWaitNs, abort_flag))
+                                kWaitNs, abort_flag))
           break;
         if (c >= nX) {
           // a row's 128 bytes are one swizzle row: process them in place in
-          // any chunk order (rotated by row to spread the banks)
-          // both rows are read into registers before any store, so that the
-          // loads are not held behind stores the compiler cannot prove apart
+          // any chunk order (rotated by row to spread the banks); both rows
+          // are read into registers before any store, so that the loads are
+          // not held behind stores the compiler cannot prove apart
           float4 v[2][8];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = e + 64 * h;
-            const float4* pa = (const float4*)(sm + stg * SB + r * 128);
+            const float4* pa = (const float4*)(sm + stg * SB + r * kRowBytes);
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[h][q] = pa[(q + r) & 7];
           }
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = e + 64 * h;
-            float4* pa = (float4*)(sm + stg * SB + r * 128);
-            float4* pl = (float4*)(sm + stg * SB + kStageA + r * 128);
+            float4* pa = (float4*)(sm + stg * SB + r * kRowBytes);
+            float4* pl = (float4*)(sm + stg * SB + kStageA + r * kRowBytes);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int j = (q + r) & 7;
@@ -589,7 +483,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int gt = row;                  // thread index inside the group
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int nblk = (s + 15) >> 4;
-    const int mis = (int)(rank & 3);
     const int bar_id = 2 + grp;
     for (int it = grp;; it += 2) {
       const long long tile = blockIdx.x + (long long)it * gridDim.x;
@@ -617,7 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int ri = 0; ri < 4; ++ri)
           if (p == growv[ri]) eq.jpiv[ri] = j;
       }
-      tc::mbar_wait_warp(&accf[grp], (uint32_t)((it >> 1) & 1), tc::globaltimer_ns() + kWaitNs,
+      tc::mbar_wait_warp(&accf[grp], (uint32_t)((it >> 1) & 1), kWaitNs,
                          abort_flag);
       // one thread's reading of the abort flag decides for the whole group
       asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");

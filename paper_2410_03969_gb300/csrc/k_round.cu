@@ -373,10 +373,15 @@ __device__ __forceinline__ int own_off(int j) {
 // exact), so that only the three operations of the step use the FP64 pipe.
 // FP64 mode takes a second step (about 1 ulp).  Arguments outside
 // [1e-30, 1e30] (checked on the bit pattern) take sqrt and divide.
-__device__ __forceinline__ double rsqrt_newton(double x, bool second) {
-  const long long xb = __double_as_longlong(x);
+__device__ __forceinline__ bool rsqrt_in_range(double x) {
   // 1e-30 < x < 1e30 on the bit pattern (positive doubles order like integers)
-  if (!(xb > 0x39b4484bfeebc2a0ll && xb < 0x46293e5939a08ceall)) return 1.0 / sqrt(x);
+  const long long xb = __double_as_longlong(x);
+  return xb > 0x39b4484bfeebc2a0ll && xb < 0x46293e5939a08ceall;
+}
+
+// The Newton-Raphson path alone, for x with rsqrt_in_range(x).
+__device__ __forceinline__ double rsqrt_core(double x, bool second) {
+  const long long xb = __double_as_longlong(x);
   const float xf = __int_as_float((int)((xb >> 29) - (896ll << 23)));
   const float rf = rsqrtf(xf);
   const double y = __longlong_as_double(((long long)__float_as_int(rf) + (896ll << 23)) << 29);
@@ -387,6 +392,11 @@ __device__ __forceinline__ double rsqrt_newton(double x, bool second) {
   if (!second) return y1;
   const double r1 = fma(-x * y1, y1, 1.0);
   return fma(0.5 * y1, r1, y1);
+}
+
+__device__ __forceinline__ double rsqrt_newton(double x, bool second) {
+  if (!rsqrt_in_range(x)) return 1.0 / sqrt(x);
+  return rsqrt_core(x, second);
 }
 
 // u < h for u >= +0 as an integer comparison of the bit patterns (FP64
@@ -410,28 +420,13 @@ __device__ __forceinline__ uint32_t map_to(const void* p, uint32_t cta) {
   return out;
 }
 
-__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
-  double v;
-  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
-  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
 // Asynchronous store into another CTA's shared memory that completes
-// `bytes` of that CTA's barrier's expected transaction count on arrival.
-__device__ __forceinline__ void st_async_f64(const void* dst, double v, uint64_t* bar,
-                                             uint32_t cta) {
+// `bytes` of that CTA's barrier's expected transaction count on arrival;
+// both addresses already mapped into the receiving CTA's window.
+__device__ __forceinline__ void st_async_f64_at(uint32_t dst, double v, uint32_t bar) {
   asm volatile(
-      "st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(
-          map_to(dst, cta)),
-      "l"(__double_as_longlong(v)), "r"(map_to(bar, cta))
+      "st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(dst),
+      "l"(__double_as_longlong(v)), "r"(bar)
       : "memory");
 }
 
@@ -453,19 +448,13 @@ __device__ __forceinline__ void arrive_expect_local(uint64_t* bar, uint32_t byte
                : "memory");
 }
 
-// mbarrier arrival on a barrier of another CTA of the cluster, releasing
-// this thread's earlier writes (and those ordered before them) cluster-wide
-__device__ __forceinline__ void arrive_remote(uint64_t* bar, uint32_t cta) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
-                   map_to(bar, cta))
-               : "memory");
-}
-
 // Bounded wait (acquire, cluster scope) for the phase of the given parity of
-// a barrier of this CTA: false once the deadline (ns of %globaltimer) passes.
+// a barrier of this CTA: false once `limit_ns` of %globaltimer have passed.
+// The clock is read only after the first test has failed.
 __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t parity,
-                                                     unsigned long long deadline) {
+                                                     unsigned long long limit_ns) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  unsigned long long deadline = 0;
   for (uint32_t n = 0;; ++n) {
     uint32_t ok;
     asm volatile(
@@ -476,18 +465,13 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t* bar, uint32_t par
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((n & 15) == 15) {
+    if (n == 0 || (n & 15) == 15) {
       unsigned long long now;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-      if (now > deadline) return false;
+      if (n == 0) deadline = now + limit_ns;
+      else if (now > deadline) return false;
     }
   }
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -505,8 +489,9 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
   __shared__ long long ub[kTMax];   // lead CTA: u_i U_i, bit pattern of a non-negative double
   __shared__ int accl[kTMax];
   __shared__ int nxt_sh[2];
-  __shared__ double inv_sh[2];
-  __shared__ __align__(8) uint64_t bars[2];  // lead: teams done; others: column published
+  __shared__ __align__(8) uint64_t bars[2];  // CTAs 1..: publication p complete in bars[p & 1]
+  __shared__ double colbuf[2][kTMax];        // lead: column n_t of H through pivot t-2, pushed
+  __shared__ __align__(8) uint64_t cbar[2];  // lead: column n_t complete in cbar[t & 1]
   __shared__ int ok_sh;
   // every CTA of the cluster reads the same state, so all take the same path
   if (st->done) return;
@@ -522,15 +507,13 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
   constexpr unsigned long long kWait = 2000000000ull;  // 2 s per wait
 
   if (tid == 0) {
-    const uint32_t cnt = lead ? (uint32_t)kRejOwners : 1u;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(&bars[0])),
-                 "r"(cnt)
-                 : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
-                     (uint32_t)__cvta_generic_to_shared(&bars[1])),
-                 "r"(cnt)
-                 : "memory");
+    // one local arrival per phase (with its expected transaction bytes);
+    // the data itself arrives by st.async
+    uint64_t* b = lead ? cbar : bars;
+    for (int i = 0; i < 2; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
+                       (uint32_t)__cvta_generic_to_shared(&b[i]))
+                   : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (!lead) arrive_expect_local(&bars[0], 4u);  // publication 0: n_0 alone
   }
@@ -568,12 +551,19 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
 
   int t = 0;
   if (lead) {
+    // lcb[0][0] and bars[0] as seen from every other CTA of the cluster
+    uint32_t lcb_c[kRejCluster - 1], bars_c[kRejCluster - 1];
+#pragma unroll
+    for (int c = 1; c < kRejCluster; ++c) {
+      lcb_c[c - 1] = map_to(&lcb[0][0], (uint32_t)c);
+      bars_c[c - 1] = map_to(&bars[0], (uint32_t)c);
+    }
     if (warp < kLeadWarps) {
       if (warp == 0) {
         const int nx = maxacc > 0 ? next_accept(0) : T;
         if (lane == 0) {
           nxt_sh[0] = nx;
-          inv_sh[0] = nx < T ? rsqrt_newton(dg[nx], fp64) : 0.0;
+          if (nx < T) arrive_expect_local(&cbar[0], 8u * (uint32_t)(T - nx));
           publish(0, nx);
         }
       }
@@ -582,63 +572,63 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
         const int n_t = nxt_sh[t & 1];
         if (n_t >= T) break;
         const double* lp = lcb[(t + 1) & 1];  // column of pivot t - 1
-        const double inv = inv_sh[t & 1];
         const double lpn = lp[n_t];
         double* lc = lcb[t & 1];
-        // column t below the pivot, from the rows' owners; warp 0 owns rows
-        // n_t+1..n_t+32, the ones the next acceptance test looks at first
+        // 1/sqrt(h) of the pivot (every lead thread forms it from dg,
+        // identically) while the rows' owners push column n_t
+        const double inv = rsqrt_newton(dg[n_t], fp64);
+        if (!wait_cluster_bounded(&cbar[t & 1], (uint32_t)((t >> 1) & 1), kWait)) {
+          if (tid == 0) atomicOr(&st->status, (int)kStTimeout);
+          break;
+        }
+        const double* hc = colbuf[t & 1];
+        // column t below the pivot; warp 0 owns rows n_t+1..n_t+32, the ones
+        // the next acceptance test looks at first
         double dwin = 0.0;
         for (int j = n_t + 1 + tid; j < T; j += 32 * kLeadWarps) {
-          const int oc = 1 + j % kRejOwners;
-          const double h = ld_cluster_f64(map_to(Hown + own_off(j) + n_t, oc));
-          const double v = fma(-lp[j], lpn, h) * inv;
+          const double v = fma(-lp[j], lpn, hc[j]) * inv;
           const double dn = fma(-v, v, dg[j]);
           dg[j] = dn;
           if (j < n_t + 1 + 32 * kLeadWarps) dwin = dn;
           lc[j] = v;
           Lw[(long long)j * kTMax + t] = v;
+          const uint32_t off = (uint32_t)(((t & 1) * kTMax + j) * 8);
+          const uint32_t boff = (uint32_t)(((t + 1) & 1) * 8);
+#pragma unroll
           for (int c = 1; c < kRejCluster; ++c)
-            st_async_f64(&lcb[t & 1][j], v, &bars[(t + 1) & 1], c);
+            st_async_f64_at(lcb_c[c - 1] + off, v, bars_c[c - 1] + boff);
         }
         if (tid == 32 * kLeadWarps - 1) {  // the pivot's own entry, h / sqrt(h)
-          const double h = ld_cluster_f64(map_to(Hown + own_off(n_t) + n_t, 1 + n_t % kRejOwners));
-          const double v = fma(-lpn, lpn, h) * inv;
+          const double v = fma(-lpn, lpn, hc[n_t]) * inv;
           lc[n_t] = v;
           Lw[(long long)n_t * kTMax + t] = v;
         }
         if (warp == 0) {
           // barrier 1: the lead warps' parts of column t are out; barrier 2:
-          // warp 0's decision is in nxt_sh / inv_sh
+          // warp 0's decision is in nxt_sh
           int nx = T;
           bool waited = false;
-          double hx = 0.0;
           if (t + 1 < maxacc) {
             const int i = n_t + 1 + lane;
             const unsigned m = __ballot_sync(0xffffffffu, i < T && accept_bits(ub[i], dwin));
             if (m) {
               const int src = __ffs(m) - 1;
               nx = n_t + 1 + src;
-              hx = __shfl_sync(0xffffffffu, dwin, src);
             } else {
               asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
               waited = true;
               nx = next_accept(n_t + 33);
-              if (nx < T) hx = dg[nx];
             }
           }
-          const double iv = nx < T ? rsqrt_newton(hx, fp64) : 0.0;
-          if (!waited) asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
-          int ok = 1;
           if (lane == 0) {
             accl[t] = n_t;
+            // column n_{t+1} will come from the rows' owners once they have
+            // n_{t+1}: expect its bytes before announcing it
+            if (nx < T) arrive_expect_local(&cbar[(t + 1) & 1], 8u * (uint32_t)(T - nx));
             publish(t + 1, nx);
-            // the other CTAs' downdate of pivot t - 1 (their iteration t) must be
-            // done before the lead reads column n_{t+1}
-            ok = wait_cluster_bounded(&bars[t & 1], (uint32_t)((t >> 1) & 1), now_ns() + kWait);
-            if (!ok) atomicOr(&st->status, (int)kStTimeout);
-            nxt_sh[(t + 1) & 1] = ok ? nx : T;
-            inv_sh[(t + 1) & 1] = iv;
+            nxt_sh[(t + 1) & 1] = nx;
           }
+          if (!waited) asm volatile("bar.sync 1, %0;" ::"r"(32 * kLeadWarps) : "memory");
           __syncwarp();
           asm volatile("bar.arrive 2, %0;" ::"r"(32 * kLeadWarps) : "memory");
         } else {
@@ -648,9 +638,9 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
       }
     }
   } else {
+    const uint32_t colbuf_lead = map_to(&colbuf[0][0], 0u), cbar_lead = map_to(&cbar[0], 0u);
     for (;; ++t) {
-      if (tid == 0) ok_sh = wait_cluster_bounded(&bars[t & 1], (uint32_t)((t >> 1) & 1),
-                                                 now_ns() + kWait)
+      if (tid == 0) ok_sh = wait_cluster_bounded(&bars[t & 1], (uint32_t)((t >> 1) & 1), kWait)
                                 ? 1
                                 : 0;
       __syncthreads();
@@ -660,6 +650,17 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
       }
       const int n_t = nxt_sh[t & 1];
       if (n_t >= T) break;
+      {
+        // push column n_t of this CTA's rows j >= n_t (downdated through
+        // pivot t - 2; the lead applies pivot t - 1 itself) into the lead's
+        // colbuf: the st.async bytes complete the lead's barrier phase, which
+        // also makes them visible there
+        const int i0 = n_t > own ? (n_t - own + kRejOwners - 1) / kRejOwners : 0;
+        const int j = own + kRejOwners * (i0 + tid);
+        if (j < T)
+          st_async_f64_at(colbuf_lead + (uint32_t)(((t & 1) * kTMax + j) * 8),
+                          Hown[own_off(j) + n_t], cbar_lead + (uint32_t)((t & 1) * 8));
+      }
       // publication t + 1 brings column t for rows n_t+1..T-1 and n_{t+1}
       if (tid == 0) arrive_expect_local(&bars[(t + 1) & 1], 8u * (uint32_t)(T - 1 - n_t) + 4u);
       if (t > 0) {
@@ -672,11 +673,7 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
           for (int l = n_t + 1 + lane; l <= j; l += 32) Hown[o + l] = fma(-lj, lp[l], Hown[o + l]);
         }
       }
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("fence.acq_rel.cluster;" ::: "memory");
-        arrive_remote(&bars[t & 1], 0);
-      }
+      __syncthreads();  // the next push reads rows this downdate wrote
     }
   }
   if (lead && tid == 0) ok_sh = t;  // pivots accepted (lead warps 4.. never ran the loop)
@@ -709,8 +706,10 @@ cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s) {
     if (n > most) most = n;
   }
   const size_t dyn = most * sizeof(double);
+  // static and dynamic shared memory together pass the 48 KiB default for
+  // T above about 200: opt in for whatever this launch needs
   static size_t attr = 0;
-  if (dyn > 48 * 1024 && dyn > attr) {
+  if (dyn > attr) {
     cudaError_t e =
         cudaFuncSetAttribute(k_reject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;

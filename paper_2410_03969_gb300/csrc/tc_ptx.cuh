@@ -65,13 +65,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete, giving up at the
-// deadline (ns of %globaltimer) or when *abort is set.  Returns true when the
-// phase completed.  After every 16 failed polls the thread checks the abort
-// flag and the clock and backs off briefly.
+// Wait for the phase with the given parity to complete, giving up after
+// `limit_ns` of %globaltimer or when *abort is set.  Returns true when the
+// phase completed.  The clock is read only once the first test has failed
+// (a read of %globaltimer is slow next to a completed test); after every 16
+// failed polls the thread checks the abort flag and the clock and backs off
+// briefly.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  unsigned long long deadline,
+                                                  unsigned long long limit_ns,
                                                   volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long deadline = globaltimer_ns() + limit_ns;
   for (uint32_t n = 0;; ++n) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((n & 15) == 15) {
@@ -87,10 +91,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 // Warp-wide bounded wait: lane 0 polls, the result is broadcast.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity,
-                                               unsigned long long deadline,
+                                               unsigned long long limit_ns,
                                                volatile int* abort) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity, deadline, abort) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity, limit_ns, abort) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   return ok != 0;
 }
@@ -110,6 +114,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Bring the box at (x, y) of a 2-D tensor map into L2 (no shared-memory
+// destination, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   (unsigned long long)map),
+               "r"(x), "r"(y)
+               : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
@@ -186,6 +199,32 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// The same, also keeping A in the tensor core's collector buffer for the
+// next MMA (which must name the same A and use mma_tf32_reuse_a).
+__device__ __forceinline__ void mma_tf32_keep_a(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// A from the collector buffer filled by the previous MMA (shared memory is
+// not read for A), releasing the buffer afterwards.
+__device__ __forceinline__ void mma_tf32_reuse_a(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                                 uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
