@@ -63,6 +63,38 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM traffic of the tensor-core column step per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum of every k_colstep_tc launch of one ncu capture of
+# `bench.py --quick --no-graph --steps 1 --warmup 1` on this workload, divided
+# by the number of launches), with the SHA-256 of the sources the capture ran.
+# When those sources have changed since, the figure no longer describes the
+# kernel and the bench reports null.  Summary: profiles/colstep_tc_mixture20_n1e5.md.
+_COLSTEP_SOURCES = ("k_colstep_tc.cu", "tc_ptx.cuh", "common.cuh", "internal.h")
+_COLSTEP_TRAFFIC = {
+    ("mixture20_n1e5", "mixed"): (
+        161941840.0, "11d733e4f5a752215bc7aabea17fb7514ea5c3c6911e26a3389bf05063a22791"),
+}
+
+
+def _colstep_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in _COLSTEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2410_03969_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _colstep_traffic(workload: str, precision: str):
+    e = _COLSTEP_TRAFFIC.get((workload, precision))
+    if e is None:
+        return None
+    try:
+        return e[0] if _colstep_sources_sha() == e[1] else None
+    except OSError:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
 
@@ -439,7 +471,7 @@ def ours_arm(args):
             achieved = sp["col_bytes"] / (col_ms / 1e3) / 1e9
             peak = peaks["hbm_gbs"]
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": _colstep_traffic(args.workload, prec),
                     "peak_source": "hbm_gbs of MEASURED_PEAKS.json (%s)" % src}
         roof.update({"kernel": "column step", "launches": nl, "avg_launch_ms": col_ms / nl,
                      "alg_bytes_per_launch": sp["col_bytes"] / nl,
