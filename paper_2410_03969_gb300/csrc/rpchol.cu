@@ -84,6 +84,9 @@ struct rpchol_ctx {
   long long host_iters = -1;  // loop bodies the host loop launched (-1: graph)
   int profile = 0;
   std::vector<ProfRec> prof;  // events of the last profiled run
+  int* gate_host = nullptr;   // profile mode: pinned, mapped release flag of the stream gate
+  int* gate_dev = nullptr;
+  int gate_gen = 0;
   int use_tc = 0;             // mixed mode: tensor-core column step
   TcMaps tc{};
 };
@@ -125,6 +128,8 @@ void release_all(rpchol_ctx* c) {
   else cudaDeviceSynchronize();
   if (c->st_host) cudaFreeHost(c->st_host);
   c->st_host = nullptr;
+  if (c->gate_host) cudaFreeHost(c->gate_host);
+  c->gate_host = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
 }
@@ -175,7 +180,6 @@ rpchol_status make_map(CUtensorMap* m, const void* base, unsigned long long inne
 // Phases of one loop-body iteration (profile-mode event slots):
 // 0 propose, 1 H, 2 Algorithm 1, 3 operand prep, 4 column step, 5 round end,
 // 6 simple-RPC GEMV, 7 simple-RPC finish.
-constexpr int kPhases = 8;
 
 struct Phase {
   int slot;
@@ -276,6 +280,19 @@ rpchol_status get_graph(rpchol_ctx* c, int plain, int T, cudaGraphExec_t* out) {
   return RPCHOL_OK;
 }
 
+// Profile mode holds the stream at a gate until a whole chunk of rounds (the
+// kernels and the events around them) is enqueued, so that the events time
+// the kernels back to back rather than the host's enqueue rate.  The gate
+// polls a pinned host flag for at most about a second.
+__global__ void k_gate(const int* flag, int target) {
+  for (int i = 0; i < 1000000; ++i) {
+    int v;
+    asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+    if (v >= target) return;
+    __nanosleep(1000);
+  }
+}
+
 void clear_prof(rpchol_ctx* c) {
   for (auto& r : c->prof) {
     cudaEventDestroy(r.a);
@@ -298,15 +315,29 @@ rpchol_status run_common(rpchol_ctx* c, int plain, long long k, int T, unsigned 
     CU(cudaGraphLaunch(ex, c->stream));
     return RPCHOL_OK;
   }
+  if (c->profile && !c->gate_host) {
+    CU(cudaHostAlloc((void**)&c->gate_host, sizeof(int), cudaHostAllocMapped));
+    *(volatile int*)c->gate_host = 0;
+    c->gate_gen = 0;
+    CU(cudaHostGetDevicePointer((void**)&c->gate_dev, c->gate_host, 0));
+  }
   // host loop: launch rounds in chunks, read the done flag between chunks
   for (long long it = 0; it < max_rounds + 1;) {
     const long long chunk = plain ? 64 : 8;
+    if (c->profile) {
+      k_gate<<<1, 1, 0, c->stream>>>(c->gate_dev, ++c->gate_gen);
+      CU(cudaGetLastError());
+    }
     for (long long j = 0; j < chunk; ++j, ++it) {
       cudaError_t e = launch_body(c, plain, T, 0ull, 0, c->stream,
                                   c->profile ? &c->prof : nullptr, it);
-      if (e != cudaSuccess) return cuda_fail(e, "round launch");
+      if (e != cudaSuccess) {
+        if (c->profile) __atomic_store_n(c->gate_host, c->gate_gen, __ATOMIC_RELEASE);
+        return cuda_fail(e, "round launch");
+      }
       c->host_iters = it + 1;
     }
+    if (c->profile) __atomic_store_n(c->gate_host, c->gate_gen, __ATOMIC_RELEASE);
     CU(cudaMemcpyAsync(c->st_host, c->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     if (c->st_host->done) break;

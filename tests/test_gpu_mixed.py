@@ -172,3 +172,30 @@ def test_many_chunks_per_tile_match_the_exact_factor_of_the_pivots(rp):
             err = np.linalg.norm(g["F"] - Fx) / np.linalg.norm(Fx)
             assert err <= 5e-4, (seed, err)
             assert st["trace_error"] == pytest.approx(tex / 40000, rel=5e-3)
+
+
+def test_profiled_run_is_the_same_run(rp):
+    """The profiled pass (host-launched rounds behind a stream gate, events
+    around every phase) runs the same kernels as the graph: same pivots,
+    bit-identical factor, and phase times that add up to no more than the
+    wall time of the run."""
+    import time
+    import torch
+    prob = workloads.Problem("laplace5", workloads.gaussian_cloud(4000, 5, 1), "laplace_l2",
+                             2.0, k=200, T=64)
+    out = {}
+    for profile in (False, True):
+        with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
+                           precision="mixed", profile=profile) as f:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f.run(prob.k, prob.T, 5).sync()
+            wall_ms = (time.perf_counter() - t0) * 1e3
+            out[profile] = (f.copy_factor(), f.stats(), wall_ms)
+    (g0, s0, _), (g1, s1, w1) = out[False], out[True]
+    assert s0["status"] == 0 and s1["status"] == 0
+    assert np.array_equal(g0["S"], g1["S"])
+    assert np.array_equal(g0["F"], g1["F"])
+    ph = s1["phase_ms"]
+    assert ph["colstep"] > 0 and ph["reject"] > 0 and ph["H"] > 0
+    assert sum(ph.values()) <= w1
