@@ -61,7 +61,7 @@ struct DevBuffers {
   long long ldB;
   float* Bs32;       // mixed mode: T_max x ldBs rows of the column-step operand
   long long ldBs;
-  double* Hpart;     // kHTilesMax x kHSplitMax x 256 partial products of H
+  double* Hpart;     // kHTilesMax x (kHSplitMax + 1) x 256: partial products of H, kernel entries
   int* hcnt;         // kHTilesMax arrival counters (zero between launches)
   double* red;       // reduction scratch (trace error)
   long long nred;

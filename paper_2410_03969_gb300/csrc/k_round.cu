@@ -219,10 +219,14 @@ cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s) {
 // products are exact in FP64).  Kernel entries by direct differences.
 // Output tiles of 16 x 16 (lower triangle of tiles; both halves of H are
 // written from the same value), one thread per entry.  FP64 throughput is
-// low on this GPU, so the rank dimension is split KS = gridDim.y ways to
-// spread the tiles over all SMs: each CTA writes a partial product, and the
-// last CTA of a tile to finish (counted with an atomic) adds the KS partials
-// in the fixed order z = 0..KS-1, so the result does not depend on timing.
+// low on this GPU, so the rank dimension is split KS = gridDim.y ways, in
+// equal parts, to spread the tiles over all SMs: each CTA writes a partial
+// product, and the last CTA of a tile to finish (counted with an atomic)
+// adds the KS partials in the fixed order z = 0..KS-1, so the result does
+// not depend on timing.  The kernel entries of a tile are shared out among
+// its KS CTAs too (entries z, z + KS, ... to CTA z, computed by its first
+// threads: an FP64 instruction costs the same with one lane active as with
+// 32), so that no CTA evaluates the kernel after all the partials are in.
 template <typename TF>
 __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* __restrict__ X,
                                               int xld, int d, int kind, double inv_sigma,
@@ -244,8 +248,8 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
   const int a0 = 16 * ta, b0 = 16 * tb;
   if (a0 >= T) return;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const long long kc = ((rank + KS - 1) / KS + 31) & ~31ll;
-  const long long m_lo = z * kc;
+  const long long kc = (rank + KS - 1) / KS;
+  const long long m_lo = z * kc < rank ? z * kc : rank;
   const long long m_hi = m_lo + kc < rank ? m_lo + kc : rank;
   // rows of this thread's two staged elements (row e >> 5, column e & 31)
   int ra[2], rb[2];
@@ -265,8 +269,29 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
       vb[q] = m < m_hi ? F[(long long)rb[q] * ldF + m] : (TF)0;
     }
   };
+  // kernel entry of H at (a, b), 1 on the diagonal of A
+  auto kval = [&](int a, int b) -> double {
+    const int pa = prop[a], pb = prop[b];
+    if (pa == pb) return 1.0;
+    const float* xa = X + (long long)pa * xld;
+    const float* xb = X + (long long)pb * xld;
+    double r2 = 0.0;
+    for (int l = 0; l < d; ++l) {
+      const double t = (double)xa[l] - (double)xb[l];
+      r2 += t * t;
+    }
+    return phi_r2<double>(kind, inv_sigma, r2);
+  };
   double acc = 0.0;
   if (m_lo < m_hi) fetch(m_lo);
+  // this CTA's share of the kernel entries (slot KS of the tile's partials),
+  // formed while the first chunk of F is in flight
+  double* P = Hpart + (long long)tile * (KS + 1) * 256;
+  if (KS > 1 && z + KS * tid < 256) {
+    const int e = z + KS * tid;
+    const int a = a0 + (e >> 4), bb = b0 + (e & 15);
+    if (a < T && bb < T && bb <= a) P[KS * 256 + e] = kval(a, bb);
+  }
   for (long long m0 = m_lo; m0 < m_hi; m0 += 32) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -276,13 +301,13 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
     }
     __syncthreads();
     if (m0 + 32 < m_hi) fetch(m0 + 32);
+    const int qn = m_hi - m0 < 32 ? (int)(m_hi - m0) : 32;
 #pragma unroll 8
-    for (int q = 0; q < 32; ++q) acc = fma(Fa[ty][q], Fb[tx][q], acc);
+    for (int q = 0; q < qn; ++q) acc = fma(Fa[ty][q], Fb[tx][q], acc);
     __syncthreads();
   }
   double sum = acc;
   if (KS > 1) {
-    double* P = Hpart + (long long)tile * KS * 256;
     P[z * 256 + tid] = acc;
     __threadfence();
     __syncthreads();
@@ -296,18 +321,7 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
   }
   const int a = a0 + ty, bcol = b0 + tx;
   if (a < T && bcol < T && bcol <= a) {
-    const int pa = prop[a], pb = prop[bcol];
-    double kv = 1.0;
-    if (pa != pb) {
-      const float* xa = X + (long long)pa * xld;
-      const float* xb = X + (long long)pb * xld;
-      double r2 = 0.0;
-      for (int l = 0; l < d; ++l) {
-        const double t = (double)xa[l] - (double)xb[l];
-        r2 += t * t;
-      }
-      kv = phi_r2<double>(kind, inv_sigma, r2);
-    }
+    const double kv = KS > 1 ? __ldcg(P + KS * 256 + tid) : kval(a, bcol);
     const double h = kv - sum;
     H[(long long)a * T + bcol] = h;
     H[(long long)bcol * T + a] = h;
