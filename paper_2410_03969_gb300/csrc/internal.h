@@ -31,7 +31,10 @@ struct TcMaps {
 
 cudaError_t launch_prep_tc(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
 cudaError_t launch_split_x(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
-cudaError_t launch_colstep_tc(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
+// The tensor-core column step also closes the round (see round_end_body):
+// `cond` / `use_cond` as for launch_round_end.
+cudaError_t launch_colstep_tc(const TcMaps& m, const struct DevBuffers& b, unsigned long long cond,
+                              int use_cond, cudaStream_t s);
 
 // Buffers of one context that the round kernels touch.  All device memory.
 struct DevBuffers {
@@ -63,6 +66,7 @@ struct DevBuffers {
   long long ldBs;
   double* Hpart;     // kHTilesMax x (kHSplitMax + 1) x 256: partial products of H, kernel entries
   int* hcnt;         // kHTilesMax arrival counters (zero between launches)
+  unsigned* ccnt;    // arrival counter of the tensor-core column step (zero between launches)
   double* red;       // reduction scratch (trace error)
   long long nred;
   DevState* st;
@@ -70,6 +74,29 @@ struct DevBuffers {
   int mixed;         // 1: F is float
   int num_sms;
 };
+
+// End of a loop-body iteration (one round of Algorithm 2, one step of
+// Algorithm 6): bookkeeping of the round, the stopping test (rank k reached,
+// or the round limit), and the WHILE condition of the graph.  One thread,
+// after every kernel of the round has finished with the state.
+__device__ __forceinline__ void round_end_body(DevState* st, unsigned long long cond, int use_cond,
+                                               long long N, int d, int bF) {
+  if (!st->done) {
+    const double n = (double)N, r = (double)st->rank, sc = (double)st->s;
+    st->col_bytes += n * (r * bF + sc * bF + 4.0 * d + 16.0);
+    st->col_flops += 2.0 * n * r * sc + n * sc * sc + 3.0 * n * d * sc;
+    st->rank += st->s;
+    st->round += 1;
+    st->proposals += st->T;
+    if (st->rank >= st->k) {
+      st->done = 1;
+    } else if (st->round >= st->max_rounds) {
+      st->done = 1;
+      st->status |= kStRoundLimit;
+    }
+  }
+  if (use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, st->done ? 0u : 1u);
+}
 
 // Thread-local message returned by rpchol_last_error (rpchol.cu).
 void set_last_error(const char* fmt, ...);

@@ -229,14 +229,14 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
 }  // namespace
 
 struct TcArgs {
-  const DevState* st;
+  DevState* st;
   float* F;
   long long ldF;
   long long N;
   const float* nrm;     // ||x||^2, FP32
   const float* nrmS;    // ||x_{S_j}||^2
   const int* Sacc;      // accepted pivots of the round
-  const float* W;       // blocked-substitution operand of the round (k_wblk)
+  const float* W;       // blocked-substitution operand of the round (formed by k_prep_tc)
   double* dvec;
   double* tile_sums;
   int* err;             // run status word
@@ -245,6 +245,10 @@ struct TcArgs {
   int xld;
   const double* L;      // compact FP64 Cholesky factor of the round
   int ldL;
+  int d;                // point dimension (round bookkeeping)
+  unsigned* ccnt;       // CTAs done with the round (zero between launches)
+  unsigned long long cond;
+  int use_cond;
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -256,10 +260,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
-  const DevState* st = a.st;
-  if (st->done) return;
+  DevState* st = a.st;
+  // a round that ended early (nothing accepted, or the run is done) is
+  // closed by one thread; otherwise the last CTA to finish closes it
+  if (st->done || st->s == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) round_end_body(st, a.cond, a.use_cond, a.N, a.d, 4);
+    return;
+  }
   const int s = st->s;
-  if (s == 0) return;
   const long long rank = st->rank;
   const Layout Lo = make_layout(s);
   const int s_pad = Lo.s_pad, nbox = Lo.nbox, SB = Lo.stage_bytes, NS = Lo.stages;
@@ -564,9 +572,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc::tc_fence_before();
   __syncthreads();
   if (warp == 1) tc::tmem_dealloc(tbase, 512);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.ccnt, 1u) == gridDim.x - 1) {
+      __threadfence();
+      round_end_body(st, a.cond, a.use_cond, a.N, a.d, 4);
+      *a.ccnt = 0u;
+    }
+  }
 }
 
-cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
+cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, unsigned long long cond,
+                              int use_cond, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_colstep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -591,6 +608,10 @@ cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t
   a.xld = b.xld;
   a.L = b.L;
   a.ldL = b.Tmax;
+  a.d = b.d;
+  a.ccnt = b.ccnt;
+  a.cond = cond;
+  a.use_cond = use_cond;
   const long long ntiles = (b.N + kBM - 1) / kBM;
   const unsigned grid = (unsigned)(ntiles < m.num_sms ? ntiles : m.num_sms);
   // the shared-memory layout depends on s, which only the device knows: the

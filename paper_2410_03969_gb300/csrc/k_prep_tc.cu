@@ -6,7 +6,8 @@
 //     columns and padded K chunks contribute nothing;
 //   - ||x_{S_j}||^2;
 //   - the blocked-substitution operand W built from the round's compact
-//     Cholesky factor L in FP64 and rounded once to FP32 (k_wblk below).
+//     Cholesky factor L in FP64 and rounded once to FP32 (wblk below), in
+//     the same launch.
 // Also the one-time split of X into head and tail planes.
 #include <cuda_runtime.h>
 
@@ -15,19 +16,18 @@
 
 namespace rpchol {
 
-__global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float* __restrict__ F,
-                                                 long long ldF, const float* __restrict__ X,
-                                                 int xld, const float* __restrict__ nrm,
-                                                 const int* __restrict__ Sacc, float* FSh,
-                                                 float* FSl, float* XSh, float* XSl, float* nrmS) {
-  if (st->done) return;
+// Row j of the B operands (one CTA per row).
+__device__ __forceinline__ void prep_row(const DevState* st, const float* __restrict__ F,
+                                         long long ldF, const float* __restrict__ X, int xld,
+                                         const float* __restrict__ nrm,
+                                         const int* __restrict__ Sacc, float* FSh, float* FSl,
+                                         float* XSh, float* XSl, float* nrmS, int j) {
   const int s = st->s;
   if (s == 0) return;
   const long long rank = st->rank;
   const long long kpad = (rank + 31) & ~31ll;
   const int s_pad = (s + 15) & ~15;
   const int rows = (s_pad + 63) & ~63;
-  const int j = blockIdx.x;
   if (j >= rows) return;
   float* fh = FSh + (long long)j * ldF;
   float* fl = FSl + (long long)j * ldF;
@@ -74,19 +74,17 @@ __global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float
 // (j0 + 16) x 16 floats at offset 256 b (b + 1) / 2, row l contiguous.
 // Rows and columns of L beyond s are taken as the identity, so padded
 // columns of G are copies of the (zero) padded columns of R.
-// Grid: blockIdx.x = b, blockIdx.y = a part of the range l < j0 (part 0
-// also writes the diagonal rows).  Each CTA forms D_b^{-1} itself, by rows
-// (row c is final once rows < c are), one step per row for the whole CTA.
-__global__ void __launch_bounds__(256) k_wblk(const DevState* st, const double* __restrict__ L,
-                                              int ldL, float* W) {
+// One CTA per block b and part of the range l < j0 (part 0 also writes the
+// diagonal rows).  Each CTA forms D_b^{-1} itself, by rows (row c is final
+// once rows < c are), one step per row for the whole CTA.
+__device__ __forceinline__ void wblk(const DevState* st, const double* __restrict__ L, int ldL,
+                                     float* W, int b, int part, int nparts) {
   __shared__ double Db[16][17];
   __shared__ double acc[16][17];
   __shared__ double Dinv[16][17];
   __shared__ double rdiag[16];
   __shared__ double Lb[16][33];  // rows j0..j0+15 of L, columns l0..l1-1
-  if (st->done) return;
   const int s = st->s;
-  const int b = blockIdx.x, part = blockIdx.y, nparts = gridDim.y;
   const int j0 = 16 * b;
   if (j0 >= s) return;
   const int per = (j0 + nparts - 1) / nparts;  // <= 32
@@ -124,6 +122,25 @@ __global__ void __launch_bounds__(256) k_wblk(const DevState* st, const double* 
     Wb[(long long)(j0 + r) * 16 + m] = (float)Dinv[m][r];
 }
 
+// One launch for both: CTAs [0, kTMax) prepare the rows of the B operands,
+// CTAs [kTMax, kTMax + 8 kTMax / 16) form the W blocks (block b, part p at
+// kTMax + 8 b + p).  The two have no data in common and run side by side.
+constexpr int kWParts = 8;
+__global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float* __restrict__ F,
+                                                 long long ldF, const float* __restrict__ X,
+                                                 int xld, const float* __restrict__ nrm,
+                                                 const int* __restrict__ Sacc, float* FSh,
+                                                 float* FSl, float* XSh, float* XSl, float* nrmS,
+                                                 const double* __restrict__ L, int ldL, float* W) {
+  if (st->done) return;
+  if (blockIdx.x < kTMax) {
+    prep_row(st, F, ldF, X, xld, nrm, Sacc, FSh, FSl, XSh, XSl, nrmS, (int)blockIdx.x);
+  } else {
+    const int i = (int)blockIdx.x - kTMax;
+    wblk(st, L, ldL, W, i / kWParts, i % kWParts, kWParts);
+  }
+}
+
 __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, float* Xl) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -134,9 +151,9 @@ __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, f
 }
 
 cudaError_t launch_prep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
-  k_prep_tc<<<kTMax, 256, 0, s>>>(b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc,
-                                  m.FShp, m.FSlp, m.XShp, m.XSlp, m.nrmS);
-  k_wblk<<<dim3(kTMax / 16, 8), 256, 0, s>>>(b.st, b.L, b.Tmax, m.Linv32);
+  k_prep_tc<<<kTMax + kWParts * (kTMax / 16), 256, 0, s>>>(
+      b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc, m.FShp, m.FSlp, m.XShp, m.XSlp,
+      m.nrmS, b.L, b.Tmax, m.Linv32);
   return cudaGetLastError();
 }
 

@@ -765,21 +765,7 @@ cudaError_t launch_gather_f64(const DevBuffers& b, int T, cudaStream_t s) {
 // ------------------------------------------------------------------ control
 __global__ void k_round_end(DevState* st, cudaGraphConditionalHandle cond, int use_cond,
                             long long N, int d, int bF) {
-  if (!st->done) {
-    const double n = (double)N, r = (double)st->rank, sc = (double)st->s;
-    st->col_bytes += n * (r * bF + sc * bF + 4.0 * d + 16.0);
-    st->col_flops += 2.0 * n * r * sc + n * sc * sc + 3.0 * n * d * sc;
-    st->rank += st->s;
-    st->round += 1;
-    st->proposals += st->T;
-    if (st->rank >= st->k) {
-      st->done = 1;
-    } else if (st->round >= st->max_rounds) {
-      st->done = 1;
-      st->status |= kStRoundLimit;
-    }
-  }
-  if (use_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+  round_end_body(st, (unsigned long long)cond, use_cond, N, d, bF);
 }
 
 cudaError_t launch_round_end(const DevBuffers& b, unsigned long long cond, int use_cond,

@@ -199,13 +199,15 @@ cudaError_t ph_prep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t 
   if (c->use_tc) return launch_prep_tc(c->tc, c->b, s);
   return launch_gather_f64(c->b, T, s);
 }
-cudaError_t ph_colstep(rpchol_ctx* c, int T, unsigned long long, int, cudaStream_t s) {
+cudaError_t ph_colstep(rpchol_ctx* c, int T, unsigned long long cond, int use_cond,
+                       cudaStream_t s) {
   if (c->precision == RPCHOL_FP64) return launch_colstep_f64(c->b, T, s);
-  if (c->use_tc) return launch_colstep_tc(c->tc, c->b, s);
+  if (c->use_tc) return launch_colstep_tc(c->tc, c->b, cond, use_cond, s);
   return launch_colstep_f32_simt(c->b, T, s);
 }
 cudaError_t ph_round_end(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
                          cudaStream_t s) {
+  if (c->use_tc) return cudaSuccess;  // the tensor-core column step closed the round
   return launch_round_end(c->b, cond, use_cond, s);
 }
 cudaError_t ph_plain_col(rpchol_ctx* c, int, unsigned long long, int, cudaStream_t s) {
@@ -484,6 +486,7 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   ALLOC(Sacc, int, kTMax);
   ALLOC(Hpart, double, (size_t)kHTilesMax * (kHSplitMax + 1) * 256);
   ALLOC(hcnt, int, kHTilesMax);
+  ALLOC(ccnt, unsigned, 1);
   ALLOC(red, double, b.nred);
   ALLOC(st, DevState, 1);
   ALLOC(Bext, double, (size_t)T_max * b.ldB);  // float rows in mixed mode
@@ -493,6 +496,8 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(F)"));
   e = cudaMemsetAsync((void*)b.X, 0, sizeof(float) * (size_t)N * b.xld, c->stream);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(X)"));
+  e = cudaMemsetAsync(b.ccnt, 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(ccnt)"));
   e = cudaMemsetAsync(b.hcnt, 0, sizeof(int) * kHTilesMax, c->stream);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(hcnt)"));
   e = cudaMemsetAsync(b.st, 0, sizeof(DevState), c->stream);
@@ -690,10 +695,12 @@ rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
   out->col_flops = st.col_flops;
   {
     // kernels of one loop body: accelerated = propose, H, Algorithm 1, operand
-    // prep (two kernels for the tensor-core step), column step, round end;
+    // prep (prep and W blocks in one launch for the tensor-core step, the
+    // gather otherwise), column step, round end (closed by the tensor-core
+    // column step itself);
     // simple = propose, GEMV, finish, step end.  The graph runs the body once
     // per round; the host loop launches whole chunks of bodies.
-    const long long per = c->last_plain ? 4 : (c->use_tc ? 7 : 6);
+    const long long per = c->last_plain ? 4 : (c->use_tc ? 5 : 6);
     const long long iters = c->host_iters >= 0 ? c->host_iters : st.round;
     out->kernel_launches = c->has_run ? 1 + per * iters : 0;
   }
@@ -791,7 +798,7 @@ int64_t rpchol_context_bytes(int64_t N, int32_t d, int64_t k_max, int32_t T_max,
   b += bf * N * ldF;                                  // F
   b += 8 * k_max + 4 * kTMax + 16 * kTMax + 4 * kTMax;  // pivots, proposals, uniforms
   b += 8 * 2LL * kTMax * kTMax + 8 * 2LL * kTMax * T_max;  // H, Lw, L, Linv
-  b += 8LL * kHTilesMax * (kHSplitMax + 1) * 256 + 4 * kHTilesMax;  // H partials, counters
+  b += 8LL * kHTilesMax * (kHSplitMax + 1) * 256 + 4 * kHTilesMax + 4;  // H partials, counters
   b += 8 * (2 + 2048 + 2) + (long long)sizeof(DevState);
   b += 8LL * T_max * (ldF + kTMax);                   // extended operand rows
   if (mixed && N >= 128) {
