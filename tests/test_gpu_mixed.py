@@ -199,3 +199,71 @@ def test_profiled_run_is_the_same_run(rp):
     ph = s1["phase_ms"]
     assert ph["colstep"] > 0 and ph["reject"] > 0 and ph["H"] > 0
     assert sum(ph.values()) <= w1
+
+
+def _rows_from_device(f, rows, rank):
+    """Rows of the device factor (FP32 in mixed mode) copied one by one with
+    cudaMemcpy, so that a factor too large for the host is never copied whole."""
+    import ctypes
+    import ctypes.util
+    cudart = None
+    for name in ("libcudart.so.13", "libcudart.so.12", ctypes.util.find_library("cudart")):
+        if not name:
+            continue
+        try:
+            cudart = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if cudart is None:
+        pytest.skip("libcudart not found")
+    F_dev, ldF, dt, r, _ = f.factor_view()
+    assert dt == 0 and r == rank  # FP32
+    out = np.zeros((len(rows), rank), dtype=np.float32)
+    cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    for i, row in enumerate(rows):
+        src = F_dev + int(row) * ldF * 4
+        rc = cudart.cudaMemcpy(out[i].ctypes.data, src, rank * 4, 2)  # device to host
+        assert rc == 0
+    return out.astype(np.float64)
+
+
+def _exact_rows(prob, S, rows):
+    """F(r,:) = A(r,S) L_S^{-*} with A(S,S) = L_S L_S^* (oracle kernel entries,
+    textbook Cholesky): the exact Nystrom factor of the pivots S."""
+    ASS = oracle.kernel_matrix(prob.X, prob.kernel, prob.sigma, rows=S, cols=S)
+    Ls = np.linalg.cholesky(ASS)
+    ArS = oracle.kernel_matrix(prob.X, prob.kernel, prob.sigma, rows=rows, cols=S)
+    return np.linalg.solve(Ls, ArS.T).T
+
+
+@pytest.mark.parametrize("make", [lambda: workloads.mixture20_n1e5(0),
+                                  lambda: workloads.unif64_n1e6(0)])
+def test_full_size_mixed_sampled_rows(rp, make):
+    """The two large workloads at their full sizes, in the mixed mode and graph
+    launch that bench.py times (mixture20: N = 1e5, k = 1000, T = 120;
+    unif64: N = 1e6, k = 4000, T = 200): rows of F sampled at random, and
+    the pivot rows, equal the exact Nystrom factor of the GPU's pivots to
+    FP32 accuracy; d of those rows equals their exact residual diagonal; the
+    reported trace error is sum(d) / N."""
+    prob = make()
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
+                       precision="mixed") as f:
+        f.run(prob.k, prob.T, 0).sync()
+        st = f.stats()
+        g = f.copy_factor(F=False, pivots=True, d=True)
+        assert st["status"] == 0 and g["rank"] == prob.k
+        S = g["S"]
+        assert len(set(S.tolist())) == prob.k
+        rng = np.random.default_rng(1)
+        rows = np.concatenate([rng.choice(prob.N, 40, replace=False), S[:4], S[-4:]])
+        Fg = _rows_from_device(f, rows, prob.k)
+    Fr = _exact_rows(prob, S, rows)
+    err = np.linalg.norm(Fg - Fr) / np.linalg.norm(Fr)
+    assert err <= 5e-4, err
+    dres = np.maximum(1.0 - np.sum(Fr * Fr, axis=1), 0.0)
+    # d is FP64 bookkeeping of FP32 columns: compare the sampled rows in sum,
+    # and row by row against the size of the row's squared norm
+    assert np.sum(g["d"][rows]) == pytest.approx(np.sum(dres), rel=5e-3, abs=1e-7)
+    assert np.max(np.abs(g["d"][rows] - dres)) <= 2e-3 * np.max(np.sum(Fr * Fr, axis=1))
+    assert st["trace_error"] == pytest.approx(np.sum(g["d"]) / prob.N, rel=1e-6, abs=1e-12)
