@@ -15,7 +15,7 @@ constexpr int kTileRows = 128;
 // Largest block size T (Algorithm 2's b).
 constexpr int kTMax = 256;
 // most ways the rank dimension of H = A(S',S') - F(S',:)F(S',:)^* is split
-constexpr int kHSplitMax = 16;
+constexpr int kHSplitMax = 8;
 constexpr int kHTilesMax = (kTMax / 16) * (kTMax / 16 + 1) / 2;
 // Leading dimensions are padded to this many elements.
 constexpr int kLdAlign = 32;
