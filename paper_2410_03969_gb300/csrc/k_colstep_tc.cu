@@ -22,9 +22,11 @@
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
 //   warps 2-3   split each fp32 F tile into TF32 head (in place) and tail
-//   warps 4-7   epilogue group 0, warps 8-11 epilogue group 1: the groups
-//               take alternate tiles; in a group, warp 4 + q (8 + q) owns
-//               TMEM lane quarter q, one thread per tile row.
+//   warps 4-11  epilogue.  With two tiles in TMEM (s_pad <= 128) warps 4-7
+//               and 8-11 form two groups taking alternate tiles, warp 4 + q
+//               (8 + q) reading TMEM lane quarter q, 4 rows per thread; with
+//               one tile in TMEM all eight work on it, two warps per lane
+//               quarter (16 lanes each), 2 rows per thread.
 // Operands stream through a ring of 2 to 4 shared-memory stages (as many as
 // fit): per stage a 128 x 32 A tile (head, tail) and an s_pad x 32 B tile
 // (head, tail), 128-byte swizzled, K-major.  For s_pad <= 128 the two
@@ -34,7 +36,8 @@
 // evaluates R = kappa - D2 block by block (16 columns), forms G_b with the
 // W blocks, stores G_b back into TMEM over the consumed D1 block (later
 // blocks read it from there) and writes it to F.  For s_pad > 128 one tile
-// holds all of TMEM and tiles alternate with their epilogues.  Every wait is
+// holds all of TMEM: tiles alternate with their epilogues, which then
+// use all eight epilogue warps.  Every wait is
 // bounded: on expiry the CTA raises the timeout bit of the run status,
 // drains its own copies and frees its TMEM.
 #include <cuda.h>
@@ -86,9 +89,11 @@ __host__ __device__ inline Layout make_layout(int s) {
   return L;
 }
 
-// ---- quad layout: thread t of a warp holds 4 rows x 4 columns of each
-// 16-column block (tmem_ld_quad16), so that the W rows it needs differ
-// between the 4 threads of a quad instead of being one broadcast value.
+// ---- quad layout: thread t of a warp holds NR rows x 4 columns of each
+// 16-column block (NR = 4: two 16-lane halves of the warp's TMEM quarter,
+// tmem_ld_quad16; NR = 2: one half, tmem_ld_half16), so that the W rows it
+// needs differ between the 4 threads of a quad instead of being one
+// broadcast value.
 struct EpiQuad {
   uint32_t d1, d2;       // TMEM D1 / D2 of the warp's lane quarter (column 0)
   const float* W;        // W blocks of the round
@@ -103,7 +108,8 @@ struct EpiQuad {
 
 // acc[ri] (columns 2cq..2cq+1 and 8+2cq..9+2cq) += sum over the 16 columns
 // kappa of block X (held across the quad) of X[ri][kappa] W(kappa, col)
-__device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float (&X)[4][4],
+template <int NR>
+__device__ __forceinline__ void quad_fma_block(float2 (&acc)[NR][2], const float (&X)[NR][4],
                                                const float* Wblk, int lane, int cq) {
   const int qbase = lane & ~3;
 #pragma unroll
@@ -113,7 +119,7 @@ __device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float 
     const float2 w01 = *(const float2*)(Wblk + 16 * kp + 2 * cq);
     const float2 w89 = *(const float2*)(Wblk + 16 * kp + 8 + 2 * cq);
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) {
+    for (int ri = 0; ri < NR; ++ri) {
       const float xv = __shfl_sync(0xffffffffu, X[ri][cj], src);
       const float2 x2 = make_float2(xv, xv);
       acc[ri][0] = __ffma2_rn(x2, w01, acc[ri][0]);
@@ -136,15 +142,15 @@ __device__ __forceinline__ float phi_fast(float inv_sigma, float r2) {
   return (1.f + t + t * t * (1.f / 3.f)) * __expf(-t);
 }
 
-template <int KIND>
-__device__ __forceinline__ void r_quad(const EpiQuad& e, int j0, const float (&D1v)[4][4],
-                                       const float (&D2v)[4][4], float (&R)[4][4]) {
+template <int KIND, int NR>
+__device__ __forceinline__ void r_quad(const EpiQuad& e, int j0, const float (&D1v)[NR][4],
+                                       const float (&D2v)[NR][4], float (&R)[NR][4]) {
 #pragma unroll
   for (int cj = 0; cj < 4; ++cj) {
     const int col = j0 + 8 * (cj >> 1) + 2 * e.cq + (cj & 1);
     const float ns = e.nrmSs[col];
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) {
+    for (int ri = 0; ri < NR; ++ri) {
       const float kv =
           col == e.jpiv[ri] ? 1.f : phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
       R[ri][cj] = col < e.s ? kv - D2v[ri][cj] : 0.f;
@@ -156,45 +162,58 @@ __device__ __forceinline__ void r_quad(const EpiQuad& e, int j0, const float (&D
 // go back into TMEM over the consumed D1 blocks.  Returns each row's
 // Kahan-compensated partial sum of squares (this thread's 4 columns of
 // every block) in rsq / rc.
-__device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (&rsq)[4],
-                                              float (&rc)[4]) {
+template <int NR>
+__device__ __forceinline__ void tmem_ld_rows(uint32_t ta, float (&v)[NR][4]) {
+  if constexpr (NR == 4) tc::tmem_ld_quad16(ta, v);
+  else tc::tmem_ld_half16(ta, v);
+}
+
+template <int NR>
+__device__ __forceinline__ void tmem_st_rows(uint32_t ta, const float (&v)[NR][4]) {
+  if constexpr (NR == 4) tc::tmem_st_quad16(ta, v);
+  else tc::tmem_st_half16(ta, v);
+}
+
+template <int NR>
+__device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (&rsq)[NR],
+                                              float (&rc)[NR]) {
   const int cq = e.cq;
   for (int bi = 0; bi < nblk; ++bi) {
     const int j0 = 16 * bi;
     const float* Wb = e.W + 128 * bi * (bi + 1);
-    float2 acc[4][2];
+    float2 acc[NR][2];
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) acc[ri][0] = acc[ri][1] = make_float2(0.f, 0.f);
+    for (int ri = 0; ri < NR; ++ri) acc[ri][0] = acc[ri][1] = make_float2(0.f, 0.f);
     for (int lb = 0; lb < bi; ++lb) {
-      float X[4][4];
-      tc::tmem_ld_quad16(e.d1 + 16 * lb, X);
+      float X[NR][4];
+      tmem_ld_rows<NR>(e.d1 + 16 * lb, X);
       quad_fma_block(acc, X, Wb + 256 * lb, e.lane, cq);
     }
     // this block of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2
-    float R[4][4];
+    float R[NR][4];
     {
-      float D1v[4][4], D2v[4][4];
-      tc::tmem_ld_quad16(e.d1 + j0, D1v);
+      float D1v[NR][4], D2v[NR][4];
+      tmem_ld_rows<NR>(e.d1 + j0, D1v);
       if (e.nF > 0) {
-        tc::tmem_ld_quad16(e.d2 + j0, D2v);
+        tmem_ld_rows<NR>(e.d2 + j0, D2v);
       } else {
 #pragma unroll
-        for (int ri = 0; ri < 4; ++ri)
+        for (int ri = 0; ri < NR; ++ri)
 #pragma unroll
           for (int cj = 0; cj < 4; ++cj) D2v[ri][cj] = 0.f;
       }
       // the kernel map, with the kind resolved outside the loop so that the
       // 16 evaluations interleave
       switch (e.kind) {
-        case 0: r_quad<0>(e, j0, D1v, D2v, R); break;
-        case 1: r_quad<1>(e, j0, D1v, D2v, R); break;
-        default: r_quad<2>(e, j0, D1v, D2v, R); break;
+        case 0: r_quad<0, NR>(e, j0, D1v, D2v, R); break;
+        case 1: r_quad<1, NR>(e, j0, D1v, D2v, R); break;
+        default: r_quad<2, NR>(e, j0, D1v, D2v, R); break;
       }
     }
     quad_fma_block(acc, R, Wb + 256 * bi, e.lane, cq);
-    float G[4][4];
+    float G[NR][4];
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) {
+    for (int ri = 0; ri < NR; ++ri) {
       G[ri][0] = acc[ri][0].x;
       G[ri][1] = acc[ri][0].y;
       G[ri][2] = acc[ri][1].x;
@@ -214,9 +233,9 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
         }
       }
     }
-    tc::tmem_st_quad16(e.d1 + j0, G);  // G_b over the consumed D1 block
+    tmem_st_rows<NR>(e.d1 + j0, G);  // G_b over the consumed D1 block
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) {
+    for (int ri = 0; ri < NR; ++ri) {
       if (e.frow[ri]) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
@@ -304,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* tptr = (uint32_t*)(tfree + 2);
   volatile int* abort_flag = (volatile int*)(tptr + 1);
   volatile int* go_flag = abort_flag + 1;      // [2], one per epilogue group
-  double* red = (double*)(small + 2048 + 512);  // [2][4]
+  double* red = (double*)(small + 2048 + 512);  // [8]: [group][quarter], or [epilogue warp]
   const float* Wsm = (const float*)(sm + Lo.w_off);
 
   for (int i = threadIdx.x; i < s_pad; i += kTcThreads) {
@@ -326,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&accf[i], 1);
-      tc::mbar_init(&tfree[i], 4);  // one arrival per warp of an epilogue group
+      tc::mbar_init(&tfree[i], nbuf == 2 ? 4 : 8);  // one arrival per epilogue warp on the tile
     }
     *abort_flag = 0;
     tc::fence_mbarrier_init();
@@ -497,8 +516,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc::mbar_arrive_warp(&conv[stg]);
       }
     }
-  } else {
-    // ------------------------------------------------ epilogue groups
+  } else if (nbuf == 2) {
+    // ------------------------------------------------ epilogue, two tiles in TMEM:
+    // groups of four warps take alternate tiles
     const int q = warp & 3;              // TMEM lane quarter of this warp
     const int grp = (warp - 4) >> 2;     // 0: warps 4-7, 1: warps 8-11
     const int row = q * 32 + lane;       // tile row = TMEM lane
@@ -543,8 +563,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc::tc_fence_after();
-      eq.d1 = tbase + lane_off + (uint32_t)((nbuf == 2 ? grp : 0) * 256);
-      eq.d2 = eq.d1 + (nbuf == 2 ? 128u : 256u);
+      eq.d1 = tbase + lane_off + (uint32_t)(grp * 256);
+      eq.d2 = eq.d1 + 128u;
       eq.W = Lo.w_resident ? Wsm : a.W;
       eq.nrmSs = nrmSs;
       eq.L = a.L;
@@ -557,9 +577,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       eq.even = (rank & 1) == 0;
       eq.inv_sigma = a.inv_sigma;
       float rsq[4] = {0.f, 0.f, 0.f, 0.f}, rc[4] = {0.f, 0.f, 0.f, 0.f};
-      epi_tile_quad(eq, nblk, rsq, rc);
+      epi_tile_quad<4>(eq, nblk, rsq, rc);
       tc::tc_fence_before();
-      tc::mbar_arrive_warp(&tfree[nbuf == 2 ? grp : 0]);  // TMEM buffer free for tile it + nbuf
+      tc::mbar_arrive_warp(&tfree[grp]);  // TMEM buffer free for tile it + 2
       // ---- row sums of G^2 across the quad (FP64), residual diagonal, tile sum
       double sq[4];
 #pragma unroll
@@ -581,6 +601,95 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
       if (gt == 0)
         a.tile_sums[tile] = red[grp * 4] + red[grp * 4 + 1] + red[grp * 4 + 2] + red[grp * 4 + 3];
+    }
+  } else {
+    // ------------------------------------------------ epilogue, one tile in TMEM:
+    // all eight warps work on it (groups taking alternate tiles would leave
+    // one idle): warp w takes TMEM lane quarter q = w & 3 (the quarter it
+    // may access) and half h = (w - 4) >> 2 of it, 16 rows, two per thread.
+    const int q = warp & 3;
+    const int h = (warp - 4) >> 2;
+    const int et = (warp - 4) * 32 + lane;  // 0..255
+    const uint32_t lane_off = (uint32_t)(q * 32 + 16 * h) << 16;
+    const int nblk = (s + 15) >> 4;
+    for (int it = 0;; ++it) {
+      const long long tile = blockIdx.x + (long long)it * gridDim.x;
+      if (tile >= ntiles) break;
+      const int buf = it % nbuf;
+      const long long row0 = tile * kBM;
+      // this thread's rows: ri -> 32 q + 16 h + lane / 4 + 8 ri
+      const int cq = lane & 3;
+      long long growv[2];
+      EpiQuad eq;
+#pragma unroll
+      for (int ri = 0; ri < 2; ++ri) {
+        growv[ri] = row0 + 32 * q + 16 * h + (lane >> 2) + 8 * ri;
+        const bool lv = growv[ri] < a.N;
+        eq.frow[ri] = lv ? a.F + growv[ri] * a.ldF + rank : nullptr;
+        eq.nr[ri] = lv ? a.nrm[growv[ri]] : 0.f;  // loaded while the accumulators fill
+        eq.jpiv[ri] = -1;
+      }
+      // threads cq = 0, 1 of a quad update d for rows ri = cq
+      const long long grow = row0 + 32 * q + 16 * h + (lane >> 2) + 8 * (cq & 1);
+      const bool live = cq < 2 && grow < a.N;
+      const double dold = live ? a.dvec[grow] : 0.0;
+      for (int j = 0; j < s; ++j) {
+        const long long p = (long long)Ss[j];
+#pragma unroll
+        for (int ri = 0; ri < 2; ++ri)
+          if (p == growv[ri]) eq.jpiv[ri] = j;
+      }
+      tc::mbar_wait_warp(&accf[it & 1], (uint32_t)((it >> 1) & 1), kWaitNs, abort_flag);
+      // one thread's reading of the abort flag decides for all eight warps
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (et == 0) go_flag[0] = *abort_flag ? 0 : 1;
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (!go_flag[0]) {
+        if (et == 0) atomicOr(a.err, (int)kStTimeout);
+        break;
+      }
+      tc::tc_fence_after();
+      eq.d1 = tbase + lane_off + (uint32_t)(buf * 256);
+      eq.d2 = eq.d1 + (nbuf == 2 ? 128u : 256u);
+      eq.W = Lo.w_resident ? Wsm : a.W;
+      eq.nrmSs = nrmSs;
+      eq.L = a.L;
+      eq.s = s;
+      eq.nF = nF;
+      eq.kind = a.kind;
+      eq.ldL = a.ldL;
+      eq.cq = cq;
+      eq.lane = lane;
+      eq.even = (rank & 1) == 0;
+      eq.inv_sigma = a.inv_sigma;
+      float rsq[2] = {0.f, 0.f}, rc[2] = {0.f, 0.f};
+      epi_tile_quad<2>(eq, nblk, rsq, rc);
+      tc::tc_fence_before();
+      tc::mbar_arrive_warp(&tfree[buf]);  // TMEM buffer free for tile it + nbuf
+      // ---- row sums of G^2 across the quad (FP64), residual diagonal, tile sum
+      double sq[2];
+#pragma unroll
+      for (int ri = 0; ri < 2; ++ri) {
+        sq[ri] = (double)rsq[ri] - (double)rc[ri];
+        sq[ri] += __shfl_xor_sync(0xffffffffu, sq[ri], 1);
+        sq[ri] += __shfl_xor_sync(0xffffffffu, sq[ri], 2);
+      }
+      const double mysq = (cq & 1) == 0 ? sq[0] : sq[1];
+      const int myjp = (cq & 1) == 0 ? eq.jpiv[0] : eq.jpiv[1];
+      double dn = 0.0;
+      if (live) {
+        const double v = dold - mysq;
+        dn = (v > 0.0 && myjp < 0) ? v : 0.0;
+        a.dvec[grow] = dn;
+      }
+      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
+      if (lane == 0) red[warp - 4] = dn;
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (et == 0) {
+        double ts = 0.0;
+        for (int w = 0; w < 8; ++w) ts += red[w];
+        a.tile_sums[tile] = ts;
+      }
     }
   }
   tc::tc_fence_before();

@@ -350,6 +350,44 @@ __device__ __forceinline__ void tmem_st_quad16(uint32_t ta, const float (&v)[4][
       : "memory");
 }
 
+// The same for one 16-lane half (lane offset already in ta): thread t holds
+// rows t/4 and t/4 + 8 of the half, columns 2 (t % 4) + {0, 1} of each
+// 8-column group.
+__device__ __forceinline__ void tmem_ld_half16(uint32_t ta, float (&v)[2][4]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0, %1, %2, %3}, [%8];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4, %5, %6, %7}, [%9];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(ta), "r"(ta + 8u)
+      : "memory");
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) v[i][2 * g + e] = __uint_as_float(r[4 * g + 2 * i + e]);
+}
+
+__device__ __forceinline__ void tmem_st_half16(uint32_t ta, const float (&v)[2][4]) {
+  uint32_t r[8];
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) r[4 * g + 2 * i + e] = __float_as_uint(v[i][2 * g + e]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%0], {%2, %3, %4, %5};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%1], {%6, %7, %8, %9};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+      "r"(ta + 8u), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+      "r"(r[7])
+      : "memory");
+}
+
 // TF32 head of an fp32 value: x rounded to nearest (ties away) at 10
 // explicit mantissa bits, low 13 bits zero, so that the tensor core sees it
 // exactly whether it truncates or rounds its inputs; the tail x - head is
