@@ -58,12 +58,24 @@ typedef enum {
     RPCHOL_ENUMERIC = 7    /* non-finite value or non-positive pivot met on the device */
 } rpchol_status;
 
-/* kappa(x, y) = phi(||x - y||_2), phi(0) = 1 so diag A = 1.
+/* kappa(x, y) = phi(r), r = ||x - y||_2 (r1 = ||x - y||_1 for LAPLACE_L1),
+ * phi(0) = 1 so diag A = 1.
  *   GAUSSIAN    exp(-r^2 / (2 sigma^2))                     (Sec. 1.2)
  *   LAPLACE_L2  exp(-r / sigma)
  *   MATERN52    (1 + sqrt5 r/sigma + 5 r^2/(3 sigma^2)) exp(-sqrt5 r/sigma)
- *                                                           (Sec. 3.2)     */
-typedef enum { RPCHOL_GAUSSIAN = 0, RPCHOL_LAPLACE_L2 = 1, RPCHOL_MATERN52 = 2 } rpchol_kernel_kind;
+ *                                                           (Sec. 3.2)
+ *   MATERN32    (1 + sqrt3 r/sigma) exp(-sqrt3 r/sigma)     (named in Sec. 4's
+ *                                         testbed; the formula is the textbook one)
+ *   LAPLACE_L1  exp(-r1 / sigma)                            (Sec. 1.2)
+ * LAPLACE_L1 has no inner-product form: its column step runs on CUDA cores
+ * (in mixed mode too), the others use the tensor-core step in mixed mode.  */
+typedef enum {
+    RPCHOL_GAUSSIAN = 0,
+    RPCHOL_LAPLACE_L2 = 1,
+    RPCHOL_MATERN52 = 2,
+    RPCHOL_MATERN32 = 3,
+    RPCHOL_LAPLACE_L1 = 4
+} rpchol_kernel_kind;
 
 /* FP64: every step in IEEE double (parity mode).
  * MIXED: F stored in FP32; the kernel-column and Schur contractions run in

@@ -28,7 +28,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KERNELS = {"gaussian": 0, "laplace_l2": 1, "matern52": 2}
+KERNELS = {"gaussian": 0, "laplace_l2": 1, "matern52": 2, "matern32": 3, "laplace_l1": 4}
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _i32p = ctypes.POINTER(ctypes.c_int32)

@@ -14,9 +14,13 @@
  *     from Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
  *     1, 2, 3" (SC'11), written from that description.
  *   - orc_kernel_entry: Gaussian (Eq. "gaussian", Sec. 1.2), Matern-5/2
- *     (Sec. 3.2) and the l2-Laplace exp(-||x-y||/sigma), all through direct
+ *     (Sec. 3.2), the l2-Laplace exp(-||x-y||/sigma), Matern-3/2 (named in
+ *     the testbed of Sec. 4 without a formula; the textbook
+ *     (1 + sqrt3 r/sigma) exp(-sqrt3 r/sigma) is taken) through direct
  *     differences sum_l (x_l - y_l)^2, as the paper's block experiments do
- *     (App. A.1, last paragraph).
+ *     (App. A.1, last paragraph), and the l1-Laplace
+ *     exp(-sum_l |x_l - y_l| / sigma) (Eq. "l1_laplace", Sec. 1.2) through
+ *     the sum of absolute differences.
  *   - orc_sample: one draw from the distribution w / sum(w) (Eq. 1.3 and
  *     the proposal step of Algorithm 2).
  *   - orc_reject_chol: RejectionSampleSubmatrix, Algorithm 1.
@@ -66,7 +70,7 @@
 #define ORC_EINVAL 1
 #define ORC_ENOMEM 2
 
-enum { ORC_GAUSSIAN = 0, ORC_LAPLACE_L2 = 1, ORC_MATERN52 = 2 };
+enum { ORC_GAUSSIAN = 0, ORC_LAPLACE_L2 = 1, ORC_MATERN52 = 2, ORC_MATERN32 = 3, ORC_LAPLACE_L1 = 4 };
 
 static int orc_threads = 1;
 
@@ -147,7 +151,8 @@ void orc_uniform_pair(uint64_t seed, uint32_t slot, uint32_t round, uint32_t ins
 }
 
 /* ---------------------------------------------------------------------- */
-/* Kernel functions phi(r) with kappa(x,x') = phi(||x - x'||).             */
+/* Kernel functions phi with kappa(x,x') = phi(q): q = ||x - x'||_2^2 for
+ * the Euclidean kernels, q = ||x - x'||_1 for the l1-Laplace.             */
 static double orc_phi_from_r2(int kind, double sigma, double r2)
 {
     if (r2 < 0.0) r2 = 0.0;
@@ -163,6 +168,12 @@ static double orc_phi_from_r2(int kind, double sigma, double r2)
         double t = sqrt(5.0) * r / sigma;
         return (1.0 + t + 5.0 * r2 / (3.0 * sigma * sigma)) * exp(-t);
     }
+    case ORC_MATERN32: {
+        double t = sqrt(3.0) * sqrt(r2) / sigma;
+        return (1.0 + t) * exp(-t);
+    }
+    case ORC_LAPLACE_L1:
+        return exp(-r2 / sigma);
     default:
         return NAN;
     }
@@ -176,12 +187,12 @@ static double orc_point_entry(int kind, double sigma, const float* X, int d, int
     if (i == j) return 1.0;
     const float* xi = X + i * (int64_t)d;
     const float* xj = X + j * (int64_t)d;
-    double r2 = 0.0;
+    double q = 0.0;
     for (int l = 0; l < d; ++l) {
         double t = (double)xi[l] - (double)xj[l];
-        r2 += t * t;
+        q += kind == ORC_LAPLACE_L1 ? fabs(t) : t * t;
     }
-    return orc_phi_from_r2(kind, sigma, r2);
+    return orc_phi_from_r2(kind, sigma, q);
 }
 
 /* A matrix seen through the submatrix access model: either kernel entries
@@ -467,7 +478,7 @@ static int make_matrix(orc_matrix* M, const float* X, int d, int kind, double si
 {
     if (N < 1) return ORC_EINVAL;
     if ((X == NULL) == (A == NULL)) return ORC_EINVAL;
-    if (X && (d < 1 || !(sigma > 0.0) || kind < 0 || kind > 2)) return ORC_EINVAL;
+    if (X && (d < 1 || !(sigma > 0.0) || kind < 0 || kind > 4)) return ORC_EINVAL;
     M->X = X;
     M->d = d;
     M->kind = kind;

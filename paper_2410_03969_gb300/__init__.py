@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librpchol.so")
 
-KERNELS = {"gaussian": 0, "laplace_l2": 1, "matern52": 2}
+KERNELS = {"gaussian": 0, "laplace_l2": 1, "matern52": 2, "matern32": 3, "laplace_l1": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EBUSY",
           6: "ECANCELLED", 7: "ENUMERIC"}

@@ -105,8 +105,13 @@ template <>
 __device__ __forceinline__ double phi_r2<double>(int kind, double inv_sigma, double r2) {
   r2 = r2 > 0.0 ? r2 : 0.0;
   if (kind == 0) return exp(-0.5 * r2 * inv_sigma * inv_sigma);
+  if (kind == 4) return exp(-r2 * inv_sigma);  // r2 holds the l1 distance
   const double r = sqrt(r2);
   if (kind == 1) return exp(-r * inv_sigma);
+  if (kind == 3) {
+    const double t = 1.7320508075688772935 * r * inv_sigma;  // sqrt(3) r / sigma
+    return (1.0 + t) * exp(-t);
+  }
   const double t = 2.2360679774997896964 * r * inv_sigma;  // sqrt(5) r / sigma
   return (1.0 + t + t * t * (1.0 / 3.0)) * exp(-t);
 }
@@ -115,10 +120,22 @@ template <>
 __device__ __forceinline__ float phi_r2<float>(int kind, float inv_sigma, float r2) {
   r2 = r2 > 0.f ? r2 : 0.f;
   if (kind == 0) return expf(-0.5f * r2 * inv_sigma * inv_sigma);
+  if (kind == 4) return expf(-r2 * inv_sigma);  // r2 holds the l1 distance
   const float r = sqrtf(r2);
   if (kind == 1) return expf(-r * inv_sigma);
+  if (kind == 3) {
+    const float t = 1.7320508075688772f * r * inv_sigma;
+    return (1.f + t) * expf(-t);
+  }
   const float t = 2.2360679774997897f * r * inv_sigma;
   return (1.f + t + t * t * (1.f / 3.f)) * expf(-t);
+}
+
+// One coordinate's share of the distance the kernel map takes: t^2 (the
+// Euclidean kernels take r^2) or |t| (the l1-Laplace takes the l1 distance).
+template <typename Real>
+__device__ __forceinline__ Real dist_term(int kind, Real t) {
+  return kind == 4 ? (t < (Real)0 ? -t : t) : t * t;
 }
 
 __host__ __device__ __forceinline__ long long round_up(long long a, long long b) {

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_colstep_simt(
             TR r2 = (TR)0;
             for (int l = 0; l < d; ++l) {
               const TR t = (TR)xa[l] - (TR)xb[l];
-              r2 += t * t;
+              r2 += dist_term(kind, t);
             }
             kv = phi_r2<TR>(kind, (TR)inv_sigma, r2);
           }

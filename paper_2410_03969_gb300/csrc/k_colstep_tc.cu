@@ -138,6 +138,10 @@ __device__ __forceinline__ float phi_fast(float inv_sigma, float r2) {
   if (KIND == 0) return __expf(-0.5f * r2 * inv_sigma * inv_sigma);
   const float r = sqrtf(r2);
   if (KIND == 1) return __expf(-r * inv_sigma);
+  if (KIND == 3) {
+    const float t = 1.7320508075688772f * r * inv_sigma;
+    return (1.f + t) * __expf(-t);
+  }
   const float t = 2.2360679774997897f * r * inv_sigma;
   return (1.f + t + t * t * (1.f / 3.f)) * __expf(-t);
 }
@@ -207,6 +211,7 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
       switch (e.kind) {
         case 0: r_quad<0, NR>(e, j0, D1v, D2v, R); break;
         case 1: r_quad<1, NR>(e, j0, D1v, D2v, R); break;
+        case 3: r_quad<3, NR>(e, j0, D1v, D2v, R); break;
         default: r_quad<2, NR>(e, j0, D1v, D2v, R); break;
       }
     }

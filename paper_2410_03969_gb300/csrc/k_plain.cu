@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_plain_col(DevState* st, const float* __
     const float* xb = X + (long long)s * xld;
     for (int l = lane; l < d; l += 32) {
       const A t = (A)xa[l] - (A)xb[l];
-      r2 += t * t;
+      r2 += dist_term(kind, t);
     }
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
   }

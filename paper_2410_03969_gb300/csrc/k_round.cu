@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
     double r2 = 0.0;
     for (int l = 0; l < d; ++l) {
       const double t = (double)xa[l] - (double)xb[l];
-      r2 += t * t;
+      r2 += dist_term(kind, t);
     }
     return phi_r2<double>(kind, inv_sigma, r2);
   };

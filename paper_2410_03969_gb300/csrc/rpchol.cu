@@ -386,7 +386,7 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
     return RPCHOL_EINVAL;
   }
   *out = nullptr;
-  if (!X || N < 1 || d < 1 || d > 4096 || !(sigma > 0.0) || kind < 0 || kind > 2 || k_max < 1 ||
+  if (!X || N < 1 || d < 1 || d > 4096 || !(sigma > 0.0) || kind < 0 || kind > 4 || k_max < 1 ||
       k_max > N || T_max < 1 || T_max > kTMax || (x_dtype != RPCHOL_DT_F32 && x_dtype != RPCHOL_DT_F64) ||
       N > (1ll << 31) - 1) {
     set_err("invalid argument: N=%lld d=%d sigma=%g kind=%d k_max=%lld T_max=%d x_dtype=%d",
@@ -524,7 +524,9 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
     // tensor-core column step: needs at least one full 128-row tile; the
     // CUDA-core FP32 path serves smaller problems (and RPCHOL_COLSTEP=simt)
     const char* env = getenv("RPCHOL_COLSTEP");
-    c->use_tc = (N >= 128) && !(env && strcmp(env, "simt") == 0);
+    // the l1-Laplace has no inner-product form, so its distances cannot come
+    // from the tensor-core contraction: the CUDA-core column step forms them
+    c->use_tc = (N >= 128) && kind != RPCHOL_LAPLACE_L1 && !(env && strcmp(env, "simt") == 0);
   }
   if (c->use_tc) {
     TcMaps& m = c->tc;

@@ -198,7 +198,7 @@ rpchol_status rpchol_server_create(int64_t mem_budget_bytes, int32_t max_slots,
 
 rpchol_status rpchol_server_submit(rpchol_server* sv, const rpchol_job* job, uint64_t* ticket) {
   if (!sv || !job || !ticket || !job->X || job->N < 1 || job->d < 1 || job->d > 4096 ||
-      job->k < 1 || job->k > job->N || !(job->sigma > 0.0) || job->kind < 0 || job->kind > 2 ||
+      job->k < 1 || job->k > job->N || !(job->sigma > 0.0) || job->kind < 0 || job->kind > 4 ||
       job->T < 0 || job->T > 256 ||
       (job->x_dtype != RPCHOL_DT_F32 && job->x_dtype != RPCHOL_DT_F64) ||
       (job->precision != RPCHOL_FP64 && job->precision != RPCHOL_MIXED)) {

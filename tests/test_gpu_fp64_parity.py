@@ -103,6 +103,8 @@ def test_gauss8_n2000_plain_matches_oracle(rp, seed):
     (640, 2, "gaussian", 0.3, 200, 256),    # T beyond the shared-memory triangle (global path)
     (257, 4, "laplace_l2", 1.0, 40, 1),     # T = 1: accelerated == simple
     (129, 6, "matern52", 1.0, 129, 16),     # k = N
+    (1000, 4, "matern32", 1.2, 80, 24),     # Matern-3/2
+    (900, 5, "laplace_l1", 5.0, 70, 20),    # l1-Laplace: direct l1 distances everywhere
 ])
 def test_shapes_and_kernels(rp, N, d, kernel, sigma, k, T):
     prob = small_problem(N, d, kernel, sigma, k)

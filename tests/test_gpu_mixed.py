@@ -34,6 +34,11 @@ CASES = [
                                            "laplace_l2", 2.0, k=200, T=64), 64),
     ("matern16", lambda: workloads.Problem("matern16", workloads.gaussian_cloud(3000, 16, 2),
                                            "matern52", 4.0, k=150, T=48), 48),
+    ("matern32", lambda: workloads.Problem("matern32", workloads.gaussian_cloud(3000, 6, 4),
+                                           "matern32", 2.0, k=150, T=40), 40),
+    # no inner-product form: the CUDA-core column step in mixed mode
+    ("laplace1", lambda: workloads.Problem("laplace1", workloads.gaussian_cloud(3000, 5, 5),
+                                           "laplace_l1", 5.0, k=150, T=40), 40),
 ]
 
 

@@ -139,11 +139,24 @@ def test_kernel_entries_direct_differences():
     assert Kl[0, 1] == pytest.approx(math.exp(-1.0), rel=1e-15)
     Km = oracle.kernel_matrix(X, "matern52", 5.0 * math.sqrt(5.0))
     assert Km[1, 0] == pytest.approx(7.0 / (3.0 * math.e), rel=1e-15)
+    Km3 = oracle.kernel_matrix(X, "matern32", 5.0 * math.sqrt(3.0))
+    assert Km3[1, 0] == pytest.approx(2.0 / math.e, rel=1e-15)
+    # l1 distance |3 - 0| + |0 - 4| = 7
+    K1 = oracle.kernel_matrix(X, "laplace_l1", 7.0)
+    assert K1[0, 1] == pytest.approx(math.exp(-1.0), rel=1e-15)
+    assert K1[0, 2] == 1.0
+    # the l1-Laplace is the product of one-dimensional Laplace kernels
+    Y = np.random.default_rng(3).standard_normal((6, 4)).astype(np.float32)
+    K1 = oracle.kernel_matrix(Y, "laplace_l1", 1.7)
+    prod = np.ones((6, 6))
+    for l in range(4):
+        prod *= np.exp(-np.abs(Y[:, None, l].astype(np.float64) - Y[None, :, l]) / 1.7)
+    assert np.allclose(K1, prod, rtol=1e-13, atol=0)
 
 
 def test_kernel_matrices_are_psd():
     X = np.random.default_rng(0).standard_normal((40, 3)).astype(np.float32)
-    for kern in ("gaussian", "laplace_l2", "matern52"):
+    for kern in ("gaussian", "laplace_l2", "matern52", "matern32", "laplace_l1"):
         K = oracle.kernel_matrix(X, kern, 1.3)
         assert np.allclose(K, K.T)
         assert np.linalg.eigvalsh(K).min() > -1e-12
