@@ -83,6 +83,10 @@ def _load():
                                       ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_int, _f64p, _i64p, _f64p, _f64p, _i64p, _i64p,
                                       _i32p, ctypes.c_int64]
+        lib.orc_rpc_block.argtypes = [_f32p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p,
+                                      ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, _f64p,
+                                      _i64p, _f64p, _i64p, _i64p, _i32p, ctypes.c_int64]
         lib.orc_fixed_pivot_factor.argtypes = [_f32p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                _f64p, ctypes.c_int64, _i64p, ctypes.c_int64,
                                                _f64p, _f64p, _f64p]
@@ -222,6 +226,27 @@ def rpc_accel(k, T, seed, X=None, kernel="gaussian", sigma=1.0, A=None, inst=0, 
     nr = rounds.value
     return {"F": F[:, :r].copy(), "S": S[:r].copy(), "d": dres, "dpre": dpre, "rank": r,
             "rounds": nr, "round_sizes": sizes[:min(nr, cap)].copy()}
+
+
+def rpc_block(k, b, seed, X=None, kernel="gaussian", sigma=1.0, A=None, inst=0, max_rounds=0):
+    """Algorithm 7 (block RPCholesky).  Returns dict(F, S, d, rank, rounds, round_sizes)."""
+    lib = _load()
+    X, d, kk, sg, A, N = _matrix_args(X, kernel, sigma, A)
+    F = np.zeros((N, max(k, 1)))
+    S = np.full(max(k, 1), -1, dtype=np.int64)
+    dres = np.zeros(N)
+    rank = ctypes.c_int64()
+    rounds = ctypes.c_int64()
+    cap = 4 * k + 64 if max_rounds <= 0 else max_rounds
+    sizes = np.zeros(cap, dtype=np.int32)
+    _check(lib.orc_rpc_block(_p(X, _f32p), d, kk, sg, _p(A, _f64p), N, k, b, max_rounds, seed,
+                             inst, _p(F, _f64p), _p(S, _i64p), _p(dres, _f64p),
+                             ctypes.byref(rank), ctypes.byref(rounds), _p(sizes, _i32p), cap),
+           "rpc_block")
+    r = rank.value
+    nr = rounds.value
+    return {"F": F[:, :r].copy(), "S": S[:r].copy(), "d": dres, "rank": r, "rounds": nr,
+            "round_sizes": sizes[:min(nr, cap)].copy()}
 
 
 def fixed_pivot_factor(S, X=None, kernel="gaussian", sigma=1.0, A=None):

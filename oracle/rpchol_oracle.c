@@ -26,6 +26,7 @@
  *   - orc_reject_chol: RejectionSampleSubmatrix, Algorithm 1.
  *   - orc_rpc_plain: simple RPCholesky, Algorithm 6 (appendix).
  *   - orc_rpc_accel: accelerated RPCholesky, Algorithm 2, calling Algorithm 1.
+ *   - orc_rpc_block: block RPCholesky, Algorithm 7 (appendix).
  *   - orc_fixed_pivot_factor: Cholesky with a given pivot order; it gives the
  *     exact Nystrom approximation A(:,S) A(S,S)^+ A(S,:) of Sec. 2.1 so that
  *     a pivot list produced elsewhere can be re-evaluated in FP64.
@@ -429,6 +430,104 @@ static int rpc_accel_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t max
     return ORC_OK;
 }
 
+/* Algorithm 7 (appendix), block RPCholesky: per round, b iid draws from
+ * d / sum(d), Unique, G = A(:,S') - F F(S',:)^*, R = Chol(G(S',:)),
+ * F(:, new) = G R^{-1}, d <- max(d - rowsumsq, 0).  Readings:
+ *   - the draws use the same Philox blocks as Algorithm 2 (slot j, round r,
+ *     proposal words), so that b = 1 meets Algorithm 6 step for step;
+ *   - Unique keeps the first draw of each index, in draw order;
+ *   - Chol is the semidefinite Cholesky in that order: a pivot whose Schur
+ *     residual is not positive gets a zero column, and the algorithm's last
+ *     line (remove zero columns) drops it; at most k - rank pivots are kept.
+ * Arguments as for rpc_accel_impl.                                        */
+static int rpc_block_impl(const orc_matrix* M, int64_t k, int32_t b, int64_t max_rounds,
+                          uint64_t seed, uint32_t inst, double* F, int64_t* S, double* d,
+                          int64_t* rank_out, int64_t* rounds_out, int32_t* round_sizes,
+                          int64_t round_sizes_cap)
+{
+    const int64_t N = M->N;
+    if (k < 0 || k > N || b < 1) return ORC_EINVAL;
+    memset(F, 0, sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
+    for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    int64_t* Su = (int64_t*)malloc(sizeof(int64_t) * (size_t)b);   /* S' after Unique */
+    double* Gs = (double*)malloc(sizeof(double) * (size_t)b * b);  /* G(S',:), then R^* */
+    int32_t* keep = (int32_t*)malloc(sizeof(int32_t) * (size_t)b);
+    if (!Su || !Gs || !keep) {
+        free(Su); free(Gs); free(keep);
+        return ORC_ENOMEM;
+    }
+    int64_t rank = 0, round = 0;
+    while (rank < k && (max_rounds <= 0 || round < max_rounds)) {
+        double W = orc_weight_total(d, N);
+        if (!(W > 0.0)) break;
+        /* b iid draws, then Unique */
+        int32_t m = 0;
+        for (int32_t j = 0; j < b; ++j) {
+            double Up;
+            orc_uniform_pair(seed, (uint32_t)j, (uint32_t)round, inst, &Up, NULL);
+            int64_t s = orc_sample(d, N, W, Up);
+            int seen = 0;
+            for (int32_t a = 0; a < m; ++a) seen |= Su[a] == s;
+            if (!seen) Su[m++] = s;
+        }
+        /* G(S',:) = A(S',S') - F(S',:) F(S',:)^* */
+        for (int32_t a = 0; a < m; ++a)
+            for (int32_t c = 0; c < m; ++c) {
+                double g = orc_entry(M, Su[a], Su[c]);
+                for (int64_t l = 0; l < rank; ++l) g -= F[Su[a] * k + l] * F[Su[c] * k + l];
+                Gs[(int64_t)a * m + c] = g;
+            }
+        /* semidefinite Cholesky, in place: the lower triangle becomes R^*
+         * on the kept columns; a dropped pivot leaves its column unused   */
+        int32_t n = 0;
+        for (int32_t i = 0; i < m; ++i) {
+            double gii = Gs[(int64_t)i * m + i];
+            if (n >= k - rank || !(gii > 0.0)) continue;
+            keep[n++] = i;
+            double piv = sqrt(gii);
+            for (int32_t j = i; j < m; ++j) Gs[(int64_t)j * m + i] /= piv;
+            for (int32_t j = i + 1; j < m; ++j)
+                for (int32_t l = i + 1; l <= j; ++l)
+                    Gs[(int64_t)j * m + l] -= Gs[(int64_t)j * m + i] * Gs[(int64_t)l * m + i];
+        }
+        if (round_sizes && round < round_sizes_cap) round_sizes[round] = n;
+        for (int32_t a = 0; a < n; ++a) S[rank + a] = Su[keep[a]];
+        /* F(r, new) = G(r, kept) R^{-1}: forward substitution with R^* */
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t r = 0; r < N; ++r) {
+            double Grow[1024];
+            double* G = Grow;
+            double* Gheap = NULL;
+            if (n > 1024) {
+                Gheap = (double*)malloc(sizeof(double) * (size_t)n);
+                G = Gheap;
+            }
+            double rsq = 0.0;
+            for (int32_t a = 0; a < n; ++a) {
+                const int64_t s = Su[keep[a]];
+                double v = orc_entry(M, r, s);
+                for (int64_t l = 0; l < rank; ++l) v -= F[r * k + l] * F[s * k + l];
+                for (int32_t c = 0; c < a; ++c)
+                    v -= G[c] * Gs[(int64_t)keep[a] * m + keep[c]];
+                G[a] = v / Gs[(int64_t)keep[a] * m + keep[a]];
+            }
+            for (int32_t a = 0; a < n; ++a) {
+                F[r * k + rank + a] = G[a];
+                rsq += G[a] * G[a];
+            }
+            double v = d[r] - rsq;
+            d[r] = v > 0.0 ? v : 0.0;
+            free(Gheap);
+        }
+        rank += n;
+        round += 1;
+    }
+    free(Su); free(Gs); free(keep);
+    *rank_out = rank;
+    if (rounds_out) *rounds_out = round;
+    return ORC_OK;
+}
+
 /* Cholesky with the given pivot order (the deterministic recursion of
  * Algorithm 6 with s_i fixed): F is N x k row-major (ld = k); d receives
  * diag(A - F F^*).  A pivot whose residual is <= 0 adds a zero column.
@@ -508,6 +607,18 @@ int orc_rpc_accel(const float* X, int d, int kind, double sigma, const double* A
     if (rc) return rc;
     return rpc_accel_impl(&M, k, T, max_rounds, seed, inst, accept_rule, F, S, dres, dpre, rank,
                           rounds, round_sizes, round_sizes_cap);
+}
+
+int orc_rpc_block(const float* X, int d, int kind, double sigma, const double* A, int64_t N,
+                  int64_t k, int32_t b, int64_t max_rounds, uint64_t seed, uint32_t inst,
+                  double* F, int64_t* S, double* dres, int64_t* rank, int64_t* rounds,
+                  int32_t* round_sizes, int64_t round_sizes_cap)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, X, d, kind, sigma, A, N);
+    if (rc) return rc;
+    return rpc_block_impl(&M, k, b, max_rounds, seed, inst, F, S, dres, rank, rounds,
+                          round_sizes, round_sizes_cap);
 }
 
 int orc_fixed_pivot_factor(const float* X, int d, int kind, double sigma, const double* A,

@@ -310,6 +310,73 @@ def test_block_size_one_equals_simple_rpcholesky():
         assert np.max(np.abs(p["F"] - a["F"])) <= 1e-13
 
 
+# ---------------------------------------------------------------- Algorithm 7
+
+
+def _draws_by_searchsorted(d, seed, b, rnd):
+    """The b proposals of one round, by numpy's searchsorted on the cumulative
+    weights (an independent restatement of the proposal map)."""
+    C = np.cumsum(d)
+    out = []
+    for j in range(b):
+        up, _ = oracle.uniform_pair(seed, j, rnd)
+        out.append(int(np.searchsorted(C, up * C[-1], side="right")))
+    return out
+
+
+def test_block_rpc_block_one_equals_simple_rpcholesky():
+    X = np.random.default_rng(19).standard_normal((300, 5)).astype(np.float32)
+    for seed in range(5):
+        p = oracle.rpc_plain(40, seed, X=X, kernel="gaussian", sigma=1.5)
+        b = oracle.rpc_block(40, 1, seed, X=X, kernel="gaussian", sigma=1.5)
+        assert list(p["S"]) == list(b["S"])
+        assert np.max(np.abs(p["F"] - b["F"])) <= 1e-13
+        assert np.max(np.abs(p["d"] - b["d"])) <= 1e-13
+
+
+@pytest.mark.parametrize("b", [3, 8, 20])
+def test_block_rpc_nystrom_identity_and_unique(b):
+    X = np.random.default_rng(20).standard_normal((70, 3)).astype(np.float32)
+    A = oracle.kernel_matrix(X, "laplace_l2", 1.5)
+    k, seed = 30, 4
+    out = oracle.rpc_block(k, b, seed, X=X, kernel="laplace_l2", sigma=1.5)
+    F, S = out["F"], out["S"]
+    assert out["rank"] == k and len(set(S.tolist())) == k
+    # Nystrom identity: F F^* = A(:,S) A(S,S)^{-1} A(S,:) (Sec. 2.1)
+    C = A[:, S]
+    nys = C @ np.linalg.solve(A[np.ix_(S, S)], C.T)
+    assert np.linalg.norm(F @ F.T - nys) / np.linalg.norm(nys) <= 1e-10
+    R = A - F @ F.T
+    assert np.max(np.abs(np.diag(R) - out["d"])) <= 1e-12
+    # round by round: the accepted pivots are the distinct draws in draw order
+    # (all residuals positive on this well-conditioned matrix), cut at rank k
+    d = np.ones(70)
+    pos = 0
+    for rnd, n in enumerate(out["round_sizes"]):
+        draws = _draws_by_searchsorted(d, seed, b, rnd)
+        uniq = list(dict.fromkeys(draws))[:k - pos]
+        assert list(S[pos:pos + n]) == uniq
+        pos += n
+        Fp = F[:, :pos]
+        d = np.maximum(1.0 - np.sum(Fp * Fp, axis=1), 0.0)
+
+
+def test_block_rpc_exact_rank_and_semidefinite_chol():
+    # rank-4 psd matrix: one round of 6 draws reaches rank 4 (any 4 distinct
+    # rows of a generic B are independent) and the factor reproduces A
+    B = np.random.default_rng(21).standard_normal((40, 4))
+    A = B @ B.T
+    out = oracle.rpc_block(4, 6, 2, A=A)
+    assert out["rank"] == 4 and out["rounds"] == 1
+    F = out["F"]
+    assert np.linalg.norm(A - F @ F.T) / np.linalg.norm(A) <= 1e-10
+    # a diagonal matrix: duplicates and zero-weight rows are never pivots
+    D = np.diag([4.0, 0.0, 1.0, 0.0, 2.0])
+    o = oracle.rpc_block(5, 8, 1, A=D)
+    assert sorted(o["S"]) == [0, 2, 4]
+    assert np.allclose(o["F"] @ o["F"].T, D, rtol=0, atol=1e-15)
+
+
 def test_zero_weight_stop_returns_lower_rank():
     # Exact exhaustion (Sec. 2.1, sum u = 0): a diagonal matrix whose pivots
     # eliminate exactly in FP64 leaves a zero residual after two pivots.
