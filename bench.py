@@ -430,6 +430,25 @@ def ours_arm(args):
         extra["speedup_vs_plain_gpu"] = statistics.median(pm) / statistics.median(step_ms)
         extra["trace_error_ratio_vs_plain_gpu"] = (sum(terr) / len(terr)) / (
             sum(pterr) / len(pterr))
+    if rank == 0 and not args.quick and args.plain_steps > 0:
+        log("block RPCholesky on the same GPU")
+        # ---- block RPCholesky (Algorithm 7, b = T): same kernels without rejection
+        bm, bterr = [], []
+        for i in range(min(args.plain_steps, 5)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f.run_block(k, T, seed_base + i)
+            b.record(stream)
+            torch.cuda.synchronize()
+            bm.append(a.elapsed_time(b))
+            bterr.append(f.stats()["trace_error"])
+        extra["block_rpc_gpu"] = {
+            "ms_p50": _pct(bm, 50), "pivots_per_s": k / (statistics.median(bm) / 1e3),
+            "trace_error_mean": sum(bterr) / len(bterr), "b": T, "steps": len(bm),
+            "precision": prec}
+        extra["trace_error_ratio_block_vs_accelerated"] = (sum(bterr) / len(bterr)) / (
+            sum(terr) / len(terr))
     if rank == 0 and not args.quick:
         log("other precision mode")
         # ---- other precision mode, for context
@@ -543,6 +562,44 @@ def ours_arm(args):
     return 0
 
 
+def colgen_measure(args):
+    """Columns of F formed per second by one block step of size b (block
+    RPCholesky to rank b: draws, H, Cholesky, fused column step), against b,
+    on N standard Gaussian points with sigma = 1 (the setting of the paper's
+    Fig. 1, which times the generation of b kernel columns)."""
+    import torch
+    import paper_2410_03969_gb300 as rp
+    rp.lib()
+    N = args.n_points or 100_000
+    rows = []
+    for kern in ("gaussian", "laplace_l1"):
+        for d in (10, 100, 1000):
+            X = torch.from_numpy(workloads.gaussian_cloud(N, d, 0)).cuda()
+            with rp.Factorizer(X, kern, 1.0, k_max=256, T_max=256,
+                               precision=args.precision) as f:
+                for b in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+                    ms, cols = [], []
+                    for i in range(8):
+                        e0, e1 = (torch.cuda.Event(enable_timing=True),
+                                  torch.cuda.Event(enable_timing=True))
+                        e0.record()
+                        f.run_block(b, b, 77 + i)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        st = f.stats()
+                        if i >= 3:
+                            ms.append(e0.elapsed_time(e1))
+                            cols.append(st["rank"])
+                    med = statistics.median(ms)
+                    rows.append({"kernel": kern, "d": d, "b": b, "ms_p50": med,
+                                 "columns_per_s": statistics.mean(cols) / (med / 1e3),
+                                 "status": st["status"]})
+            del X
+    print(json.dumps({"metric": "columns_per_s_vs_block_size", "N": N,
+                      "precision": args.precision, "rows": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,7 +623,11 @@ def main():
                     help="host-driven round loop (one launch per kernel), e.g. for ncu")
     ap.add_argument("--fp64-peak", type=float, default=1.194,
                     help="FP64 FMA peak (TFLOP/s) measured on GB300 by an FMA-loop probe")
+    ap.add_argument("--colgen", action="store_true",
+                    help="columns per second against the block size (no bench line)")
     args = ap.parse_args()
+    if args.colgen:
+        return colgen_measure(args)
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)

@@ -110,7 +110,8 @@ typedef struct {
     int64_t proposals;       /* pivots proposed in total */
     int64_t accepted;        /* pivots accepted (== rank) */
     int32_t status;          /* rpchol_status of the last run's device work */
-    int32_t plain;           /* 1 if the last run was simple RPCholesky */
+    int32_t plain;           /* algorithm of the last run: 0 accelerated, 1 simple
+                                RPCholesky, 2 block RPCholesky */
     double residual_trace;   /* sum of the clamped residual diagonal d */
     double trace_error;      /* tr(A - F F^*) / tr(A) from F itself, FP64
                                 accumulation (filled by rpchol_stats) */
@@ -163,6 +164,17 @@ rpchol_status rpchol_run(rpchol_ctx* ctx, int64_t k, int32_t T, uint64_t seed);
 /* Simple RPCholesky (Algorithm 6) to rank k on the same context: the GPU
  * baseline.  Asynchronous.                                                */
 rpchol_status rpchol_run_plain(rpchol_ctx* ctx, int64_t k, uint64_t seed);
+
+/* Block RPCholesky (Algorithm 7, appendix): each round draws b pivots iid
+ * from the residual diagonal (the same draws as rpchol_run with T = b),
+ * keeps the first draw of each index (Unique), and accepts every kept draw
+ * whose Schur residual in the FP64 Cholesky of A(S',S') - F(S',:)F(S',:)*
+ * is positive, in draw order (a non-positive residual is a zero column,
+ * which the algorithm's last line removes); the round that would pass k
+ * stops at k.  Same kernels as rpchol_run with the acceptance test of
+ * Algorithm 1 replaced; same stopping rules, status and outputs.
+ * 1 <= k <= k_max, 1 <= b <= T_max.  Asynchronous.                       */
+rpchol_status rpchol_run_block(rpchol_ctx* ctx, int64_t k, int32_t b, uint64_t seed);
 
 /* Wait for the context's stream; returns the device-side status of the
  * last run (OK, ETIMEOUT when the round limit was reached, ENUMERIC).    */

@@ -64,6 +64,8 @@ _SIGNATURES = [
     ("rpchol_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                   ctypes.c_uint64]),
     ("rpchol_run_plain", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64]),
+    ("rpchol_run_block", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.c_uint64]),
     ("rpchol_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("rpchol_factor", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                      ctypes.POINTER(ctypes.c_int64),
@@ -163,8 +165,8 @@ class _TorchAllocator:
 
 class Factorizer:
     """One rpchol context: the points are copied to the device once, then
-    ``run`` (accelerated RPCholesky) and ``run_plain`` (simple RPCholesky)
-    factorise K(X, X) to rank k on the device."""
+    ``run`` (accelerated RPCholesky), ``run_plain`` (simple RPCholesky) and
+    ``run_block`` (block RPCholesky) factorise K(X, X) to rank k on the device."""
 
     def __init__(self, X, kernel: str, sigma: float, k_max: int, T_max: int = 256,
                  precision: str = "fp64", instance: int = 0, use_graph: bool = True,
@@ -220,6 +222,11 @@ class Factorizer:
     def run_plain(self, k: int, seed: int):
         _check(lib().rpchol_run_plain(self._ctx, int(k), int(seed) & (2**64 - 1)),
                "rpchol_run_plain")
+        return self
+
+    def run_block(self, k: int, b: int, seed: int):
+        _check(lib().rpchol_run_block(self._ctx, int(k), int(b), int(seed) & (2**64 - 1)),
+               "rpchol_run_block")
         return self
 
     def sync(self):

@@ -39,7 +39,8 @@ struct DevState {
   int done;              // 1 once the run has stopped
   int status;            // StatusBits
   int plain;             // 1 for simple RPCholesky
-  int pad0;
+  int block;             // 1 for block RPCholesky (Algorithm 7): Algorithm 1 accepts every
+                         // first draw of an index whose Schur residual is positive
   unsigned long long seed;
   unsigned int instance;
   unsigned int pad1;
@@ -57,7 +58,7 @@ struct RunParams {
   long long max_rounds;  // round limit
   unsigned long long seed;
   int T;                 // proposals per round
-  int plain;             // 1: simple RPCholesky
+  int plain;             // 1: simple RPCholesky, 2: block RPCholesky, 0: accelerated
   unsigned instance;     // Philox counter word 3
   int pad;
 };

@@ -24,6 +24,30 @@ constexpr int BN = 32;   // columns per block of G
 constexpr int BK = 8;    // reduction chunk (static shared memory stays under 48 KB)
 }  // namespace
 
+// q(i, j) += sum over the kn staged coordinates of |a - b| (L1: kind 4, the
+// l1-Laplace) or (a - b)^2, coordinates in increasing order
+template <bool L1, typename TR>
+__device__ __forceinline__ void dist_tile(TR (&q)[4][4], const TR (*As)[BM + 1],
+                                          const TR (*Bs)[BN + 1], int ty, int tx, int kn) {
+#pragma unroll
+  for (int kk = 0; kk < BK; ++kk) {
+    if (kk < kn) {
+      TR a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const TR t = a[i] - b[j];
+          q[i][j] += L1 ? (t < (TR)0 ? -t : t) : t * t;
+        }
+    }
+  }
+}
+
 // TR = double: the FP64 parity mode.  TR = float: the CUDA-core FP32 path of
 // mixed mode (F in FP32, FP32 FMA with FP32 accumulation; L is rounded to
 // FP32; d stays FP64 and the squared row norms are accumulated in FP64).
@@ -81,6 +105,33 @@ __global__ void __launch_bounds__(256) k_colstep_simt(
       }
       __syncthreads();
     }
+    // distances q(x_r, x_{S_c}) = sum_l dist_term(x_rl - x_{S_c} l), tiled like
+    // the contraction above (X rows and X(S_c) staged BK coordinates at a
+    // time); every q accumulates over l in increasing order
+    TR q[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) q[i][j] = (TR)0;
+    for (int l0 = 0; l0 < d; l0 += BK) {
+#pragma unroll
+      for (int qq = 0; qq < 4; ++qq) {
+        const int e = tid + 256 * qq;
+        const int r = e >> 3, kk = e & 7;
+        const long long gr = row0 + r;
+        As[kk][r] = (gr < N && l0 + kk < d) ? (TR)X[gr * xld + l0 + kk] : (TR)0;
+      }
+      {
+        const int j = tid >> 3, kk = tid & 7;
+        Bs[kk][j] = (c0 + j < s && l0 + kk < d) ? (TR)X[(long long)Sacc[c0 + j] * xld + l0 + kk]
+                                                : (TR)0;
+      }
+      __syncthreads();
+      const int kn = d - l0 < BK ? d - l0 : BK;
+      if (kind == 4) dist_tile<true>(q, As, Bs, ty, tx, kn);
+      else dist_tile<false>(q, As, Bs, ty, tx, kn);
+      __syncthreads();
+    }
     // R'(r, c) = kappa(x_r, x_{S_c}) - acc
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -91,17 +142,7 @@ __global__ void __launch_bounds__(256) k_colstep_simt(
         TR v = (TR)0;
         if (gr < N && c < s) {
           const int p = Sacc[c];
-          TR kv = (TR)1;
-          if ((long long)p != gr) {
-            const float* xa = X + gr * xld;
-            const float* xb = X + (long long)p * xld;
-            TR r2 = (TR)0;
-            for (int l = 0; l < d; ++l) {
-              const TR t = (TR)xa[l] - (TR)xb[l];
-              r2 += dist_term(kind, t);
-            }
-            kv = phi_r2<TR>(kind, (TR)inv_sigma, r2);
-          }
+          const TR kv = (long long)p != gr ? phi_r2<TR>(kind, (TR)inv_sigma, q[i][j]) : (TR)1;
           v = kv - acc[i][j];
         }
         Rb[ty * 4 + i][tx * 4 + j] = v;

@@ -33,7 +33,8 @@ __device__ __forceinline__ void reset_run(DevState* st, double* dvec, double* ti
     st->s = 0;
     st->done = 0;
     st->status = 0;
-    st->plain = plain;
+    st->plain = plain == 1;
+    st->block = plain == 2;
     st->seed = seed;
     st->instance = inst;
     st->W = 0.0;
@@ -532,9 +533,21 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
     if (!lead) arrive_expect_local(&bars[0], 4u);  // publication 0: n_0 alone
   }
   if (lead) {
+    const bool block = st->block != 0;
     for (int i = tid; i < T; i += nt) {
       dg[i] = H[(long long)i * T + i];
-      const long long u = __double_as_longlong(uprop[i] * uacc[i]);
+      long long u;
+      if (block) {
+        // Algorithm 7: Unique keeps the first draw of each index (threshold
+        // +inf: never accepted) and the Cholesky of H takes every other draw
+        // whose Schur residual is positive (threshold +0)
+        const int pi = prop[i];
+        bool dup = false;
+        for (int j = 0; j < i; ++j) dup |= prop[j] == pi;
+        u = dup ? 0x7ff0000000000000ll : 0;
+      } else {
+        u = __double_as_longlong(uprop[i] * uacc[i]);
+      }
       ub[i] = u < 0 ? 0 : u;  // -0 -> +0
       lcb[1][i] = 0.0;        // "column -1": no downdate before pivot 0
     }

@@ -303,10 +303,13 @@ void clear_prof(rpchol_ctx* c) {
   c->prof.clear();
 }
 
-rpchol_status run_common(rpchol_ctx* c, int plain, long long k, int T, unsigned long long seed) {
+// mode 0: accelerated (Algorithm 2), 1: simple (Algorithm 6), 2: block (Algorithm 7, the
+// accelerated loop body with the acceptance rule switched in the device state)
+rpchol_status run_common(rpchol_ctx* c, int mode, long long k, int T, unsigned long long seed) {
+  const int plain = mode == 1;
   const long long max_rounds = plain ? 2 * k + 64 : 4 * k + 64;
   clear_prof(c);
-  CU(launch_reset(c->b, k, T, seed, c->instance, plain, max_rounds, c->stream));
+  CU(launch_reset(c->b, k, T, seed, c->instance, mode, max_rounds, c->stream));
   c->last_plain = plain;
   c->has_run = 1;
   c->host_iters = -1;
@@ -585,6 +588,15 @@ rpchol_status rpchol_run(rpchol_ctx* c, int64_t k, int32_t T, uint64_t seed) {
   return run_common(c, 0, k, T, seed);
 }
 
+rpchol_status rpchol_run_block(rpchol_ctx* c, int64_t k, int32_t b, uint64_t seed) {
+  g_err[0] = 0;
+  if (!c || k < 1 || k > c->k_max || b < 1 || b > c->b.Tmax) {
+    set_err("invalid argument: k=%lld b=%d", (long long)k, b);
+    return RPCHOL_EINVAL;
+  }
+  return run_common(c, 2, k, b, seed);
+}
+
 rpchol_status rpchol_run_plain(rpchol_ctx* c, int64_t k, uint64_t seed) {
   g_err[0] = 0;
   if (!c || k < 1 || k > c->k_max) {
@@ -690,7 +702,7 @@ rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
   out->proposals = st.proposals;
   out->accepted = st.rank;
   out->status = (int32_t)status_of(st);
-  out->plain = st.plain;
+  out->plain = st.plain ? 1 : (st.block ? 2 : 0);
   out->residual_trace = host[1];
   out->trace_error = host[0] / (double)c->b.N;  // tr A = N (phi(0) = 1)
   out->col_bytes = st.col_bytes;

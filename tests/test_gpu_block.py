@@ -1,0 +1,123 @@
+"""Block RPCholesky (Algorithm 7) on the GPU against the FP64 oracle.
+
+FP64 mode: the pivot sequences must be identical (both sides draw the same
+Philox stream and take Unique in draw order); a divergence is tolerated only
+at a near-tie of the proposal map (running sum within 1e-12 W of U W).  F must
+agree to 1e-10 relative Frobenius error and d to 1e-12.  Mixed mode: the
+first round is identical, the factor is the exact Nystrom factor of the GPU's
+own pivots to FP32 accuracy, and d is diag(A - FF*) of the GPU's F.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+F_TOL = 1e-10
+D_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2410_03969_gb300 as rp
+    rp.lib()
+    return rp
+
+
+def near_tie_at_divergence(X, kernel, sigma, b, seed, S_gpu, S_orc, sizes):
+    p = next(i for i in range(min(len(S_gpu), len(S_orc))) if S_gpu[i] != S_orc[i])
+    rnd = int(np.searchsorted(np.cumsum(sizes), p, side="right"))
+    pre = int(np.sum(sizes[:rnd]))
+    d = (oracle.rpc_block(pre, b, seed, X=X, kernel=kernel, sigma=sigma, max_rounds=rnd)["d"]
+         if rnd > 0 else np.ones(X.shape[0]))
+    C = np.cumsum(d)
+    W = float(np.sum(d))
+    for j in range(b):
+        up, _ = oracle.uniform_pair(seed, j, rnd)
+        if np.min(np.abs(C - up * W)) <= 1e-12 * W:
+            return True
+    return False
+
+
+def run_block(rp, X, kernel, sigma, k, b, seed, precision="fp64", T_max=None):
+    with rp.Factorizer(X, kernel, sigma, k_max=k, T_max=T_max or b, precision=precision) as f:
+        f.run_block(k, b, seed).sync()
+        g = f.copy_factor()
+        st = f.stats()
+    assert st["status"] == 0 and st["plain"] == 2
+    return g, st
+
+
+FP64_CASES = [
+    # N, d, kernel, sigma, k, b, seed
+    (2000, 8, "gaussian", 3.0, 200, 20, 0),
+    (2000, 8, "gaussian", 3.0, 200, 20, 1),
+    (1500, 4, "laplace_l2", 2.0, 150, 1, 2),      # b = 1: Algorithm 6's pivots
+    (1200, 5, "matern52", 2.5, 180, 64, 3),       # several tiles of H, ragged last round
+    (300, 3, "gaussian", 0.4, 120, 128, 4),       # many duplicate draws per round
+    (900, 5, "laplace_l1", 5.0, 70, 24, 5),       # CUDA-core column step
+    (129, 6, "matern32", 1.0, 129, 40, 6),        # k = N
+]
+
+
+@pytest.mark.parametrize("N,d,kernel,sigma,k,b,seed", FP64_CASES)
+def test_block_fp64_matches_oracle(rp, N, d, kernel, sigma, k, b, seed):
+    X = workloads.gaussian_cloud(N, d, seed + 10)
+    g, st = run_block(rp, X, kernel, sigma, k, b, seed)
+    o = oracle.rpc_block(k, b, seed, X=X, kernel=kernel, sigma=sigma)
+    if g["rank"] != o["rank"] or not np.array_equal(g["S"], o["S"]):
+        assert near_tie_at_divergence(X, kernel, sigma, b, seed, g["S"], o["S"],
+                                      o["round_sizes"]), "pivot divergence outside the margin"
+        return
+    assert st["rounds"] == o["rounds"]
+    err = np.linalg.norm(g["F"] - o["F"]) / max(np.linalg.norm(o["F"]), 1e-300)
+    assert err <= F_TOL, err
+    assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
+
+
+def test_block_one_equals_simple_rpcholesky_on_gpu(rp):
+    X = workloads.gaussian_cloud(1000, 5, 7)
+    with rp.Factorizer(X, "gaussian", 2.0, k_max=60, T_max=4) as f:
+        f.run_block(60, 1, 11).sync()
+        a = f.copy_factor()
+        f.run_plain(60, 11).sync()
+        p = f.copy_factor()
+    assert np.array_equal(a["S"], p["S"])
+    assert np.linalg.norm(a["F"] - p["F"]) <= 1e-12 * np.linalg.norm(p["F"])
+
+
+def test_block_rounds_accept_unique_draws(rp):
+    # rank per round = number of distinct draws (well-conditioned matrix),
+    # and no pivot appears twice
+    X = workloads.gaussian_cloud(400, 4, 8)
+    k, b = 300, 96
+    g, st = run_block(rp, X, "laplace_l2", 1.0, k, b, 9)
+    o = oracle.rpc_block(k, b, 9, X=X, kernel="laplace_l2", sigma=1.0)
+    assert len(set(g["S"].tolist())) == g["rank"] == k
+    assert st["proposals"] == b * st["rounds"]
+    assert np.array_equal(g["S"], o["S"])
+
+
+@pytest.mark.parametrize("N,d,kernel,sigma,k,b", [
+    (6000, 10, "gaussian", 3.0, 300, 64),
+    (5000, 16, "matern52", 4.0, 256, 120),
+])
+def test_block_mixed_mode(rp, N, d, kernel, sigma, k, b):
+    X = workloads.gaussian_cloud(N, d, 12)
+    g, st = run_block(rp, X, kernel, sigma, k, b, 13, precision="mixed")
+    assert g["rank"] == k and len(set(g["S"].tolist())) == k
+    o = oracle.rpc_block(k, b, 13, X=X, kernel=kernel, sigma=sigma, max_rounds=1)
+    s0 = o["rank"]
+    assert np.array_equal(g["S"][:s0], o["S"])  # first round: no FP32 factor yet
+    Fe, de, te = oracle.fixed_pivot_factor(g["S"], X=X, kernel=kernel, sigma=sigma)
+    err = np.linalg.norm(g["F"] - Fe) / np.linalg.norm(Fe)
+    assert err <= 5e-4, err
+    F = g["F"]
+    dd = 1.0 - np.sum(F * F, axis=1)
+    assert np.max(np.abs(np.maximum(dd, 0.0) - g["d"])) <= 2e-3
+    assert abs(st["trace_error"] - te / N) <= 5e-3 * te / N + 1e-9
