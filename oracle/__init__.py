@@ -87,6 +87,10 @@ def _load():
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, _f64p,
                                       _i64p, _f64p, _i64p, _i64p, _i32p, ctypes.c_int64]
+        lib.orc_rpc_lowmem.argtypes = [_f32p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, _f64p,
+                                       _i64p, _f64p, _i64p, _i64p]
         lib.orc_fixed_pivot_factor.argtypes = [_f32p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                _f64p, ctypes.c_int64, _i64p, ctypes.c_int64,
                                                _f64p, _f64p, _f64p]
@@ -247,6 +251,24 @@ def rpc_block(k, b, seed, X=None, kernel="gaussian", sigma=1.0, A=None, inst=0, 
     nr = rounds.value
     return {"F": F[:, :r].copy(), "S": S[:r].copy(), "d": dres, "rank": r, "rounds": nr,
             "round_sizes": sizes[:min(nr, cap)].copy()}
+
+
+def rpc_lowmem(k, T, seed, X=None, kernel="gaussian", sigma=1.0, A=None, inst=0, max_rounds=0):
+    """Algorithm 3 (low-memory accelerated RPCholesky).  Returns dict(L (rank x rank, lower
+    triangular, A(S,S) = L L^*), S, d, rank, rounds)."""
+    lib = _load()
+    X, d, kk, sg, A, N = _matrix_args(X, kernel, sigma, A)
+    L = np.zeros((max(k, 1), max(k, 1)))
+    S = np.full(max(k, 1), -1, dtype=np.int64)
+    dres = np.zeros(N)
+    rank = ctypes.c_int64()
+    rounds = ctypes.c_int64()
+    _check(lib.orc_rpc_lowmem(_p(X, _f32p), d, kk, sg, _p(A, _f64p), N, k, T, max_rounds, seed,
+                              inst, _p(L, _f64p), _p(S, _i64p), _p(dres, _f64p),
+                              ctypes.byref(rank), ctypes.byref(rounds)), "rpc_lowmem")
+    r = rank.value
+    return {"L": L[:r, :r].copy(), "S": S[:r].copy(), "d": dres, "rank": r,
+            "rounds": rounds.value}
 
 
 def fixed_pivot_factor(S, X=None, kernel="gaussian", sigma=1.0, A=None):

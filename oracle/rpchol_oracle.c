@@ -27,6 +27,8 @@
  *   - orc_rpc_plain: simple RPCholesky, Algorithm 6 (appendix).
  *   - orc_rpc_accel: accelerated RPCholesky, Algorithm 2, calling Algorithm 1.
  *   - orc_rpc_block: block RPCholesky, Algorithm 7 (appendix).
+ *   - orc_rpc_lowmem: the low-memory form of Algorithm 2, Algorithm 3
+ *     (Sec. 2.4): pivots and the k x k Cholesky factor of A(S,S) only.
  *   - orc_fixed_pivot_factor: Cholesky with a given pivot order; it gives the
  *     exact Nystrom approximation A(:,S) A(S,S)^+ A(S,:) of Sec. 2.1 so that
  *     a pivot list produced elsewhere can be re-evaluated in FP64.
@@ -528,6 +530,124 @@ static int rpc_block_impl(const orc_matrix* M, int64_t k, int32_t b, int64_t max
     return ORC_OK;
 }
 
+/* Algorithm 3, the low-memory form of Algorithm 2: no N x k factor is kept,
+ * only the pivots S and the Cholesky factor L of A(S,S) (k x k, row-major,
+ * leading dimension k).  Per round:
+ *   Step 1: the same T draws as Algorithm 2 (same Philox blocks);
+ *   Step 2: H = A(S',S') - Y^* Y with Y = L^{-1} A(S,S') (forward
+ *           substitution), then Algorithm 1 on H;
+ *   Step 3: for every row r (the listing's row chunks cover all N rows):
+ *           g = A(r,S_i) - A(r,S_old) M with M = L^{-*} Y(:,acc) formed once
+ *           per round (back substitution), G(r,:) = g L_i^{-*} (forward
+ *           substitution with L_i), u(r) -= |G(r,:)|^2;
+ *           L <- [L 0; Y(:,acc)^* L_i]; u <- max(u, 0).
+ * d receives u; Lout the k x k factor (zero beyond rank).                 */
+static int rpc_lowmem_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t max_rounds,
+                           uint64_t seed, uint32_t inst, double* Lout, int64_t* S, double* d,
+                           int64_t* rank_out, int64_t* rounds_out)
+{
+    const int64_t N = M->N;
+    if (k < 0 || k > N || T < 1) return ORC_EINVAL;
+    const int64_t kk = k > 0 ? k : 1;
+    memset(Lout, 0, sizeof(double) * (size_t)kk * (size_t)kk);
+    for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    int64_t* prop = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
+    double* u = (double*)malloc(sizeof(double) * (size_t)T);
+    double* ua = (double*)malloc(sizeof(double) * (size_t)T);
+    double* H = (double*)malloc(sizeof(double) * (size_t)T * T);
+    double* Li = (double*)malloc(sizeof(double) * (size_t)T * T);
+    int32_t* acc = (int32_t*)malloc(sizeof(int32_t) * (size_t)T);
+    double* Y = (double*)malloc(sizeof(double) * (size_t)T * kk);   /* Y(:,j) at Y + j*k */
+    double* Mm = (double*)malloc(sizeof(double) * (size_t)T * kk);  /* M(:,a) at Mm + a*k */
+    if (!prop || !u || !ua || !H || !Li || !acc || !Y || !Mm) {
+        free(prop); free(u); free(ua); free(H); free(Li); free(acc); free(Y); free(Mm);
+        return ORC_ENOMEM;
+    }
+    int64_t rank = 0, round = 0;
+    while (rank < k && (max_rounds <= 0 || round < max_rounds)) {
+        double W = orc_weight_total(d, N);
+        if (!(W > 0.0)) break;
+        for (int32_t j = 0; j < T; ++j) {
+            double Up, Ua;
+            orc_uniform_pair(seed, (uint32_t)j, (uint32_t)round, inst, &Up, &Ua);
+            prop[j] = orc_sample(d, N, W, Up);
+            u[j] = d[prop[j]];
+            ua[j] = Ua;
+        }
+        /* Y(:,j) = L^{-1} A(S, s'_j) */
+        for (int32_t j = 0; j < T; ++j) {
+            double* y = Y + (int64_t)j * kk;
+            for (int64_t m = 0; m < rank; ++m) {
+                double v = orc_entry(M, S[m], prop[j]);
+                for (int64_t l = 0; l < m; ++l) v -= Lout[m * kk + l] * y[l];
+                y[m] = v / Lout[m * kk + m];
+            }
+        }
+        for (int32_t a = 0; a < T; ++a)
+            for (int32_t c = 0; c < T; ++c) {
+                double h = orc_entry(M, prop[a], prop[c]);
+                for (int64_t m = 0; m < rank; ++m) h -= Y[(int64_t)a * kk + m] * Y[(int64_t)c * kk + m];
+                H[(int64_t)a * T + c] = h;
+            }
+        int32_t n = 0;
+        int rc = orc_reject_chol(H, T, u, ua, (int32_t)(k - rank), acc, Li, &n);
+        if (rc != ORC_OK) {
+            free(prop); free(u); free(ua); free(H); free(Li); free(acc); free(Y); free(Mm);
+            return rc;
+        }
+        /* M(:,a) = L^{-*} Y(:, acc_a) */
+        for (int32_t a = 0; a < n; ++a) {
+            const double* y = Y + (int64_t)acc[a] * kk;
+            double* z = Mm + (int64_t)a * kk;
+            for (int64_t m = rank - 1; m >= 0; --m) {
+                double v = y[m];
+                for (int64_t l = m + 1; l < rank; ++l) v -= Lout[l * kk + m] * z[l];
+                z[m] = v / Lout[m * kk + m];
+            }
+        }
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t r = 0; r < N; ++r) {
+            double gbuf[1024];
+            double* g = gbuf;
+            double* gheap = NULL;
+            if (n > 1024) {
+                gheap = (double*)malloc(sizeof(double) * (size_t)n);
+                g = gheap;
+            }
+            for (int32_t a = 0; a < n; ++a) {
+                double v = orc_entry(M, r, prop[acc[a]]);
+                for (int64_t m = 0; m < rank; ++m)
+                    v -= orc_entry(M, r, S[m]) * Mm[(int64_t)a * kk + m];
+                g[a] = v;
+            }
+            double rsq = 0.0;
+            for (int32_t a = 0; a < n; ++a) {
+                double v = g[a];
+                for (int32_t c = 0; c < a; ++c) v -= g[c] * Li[(int64_t)a * T + c];
+                g[a] = v / Li[(int64_t)a * T + a];
+                rsq += g[a] * g[a];
+            }
+            double v = d[r] - rsq;
+            d[r] = v > 0.0 ? v : 0.0;
+            free(gheap);
+        }
+        /* L <- [L 0; Y(:,acc)^* L_i] */
+        for (int32_t a = 0; a < n; ++a) {
+            for (int64_t m = 0; m < rank; ++m)
+                Lout[(rank + a) * kk + m] = Y[(int64_t)acc[a] * kk + m];
+            for (int32_t c = 0; c <= a; ++c)
+                Lout[(rank + a) * kk + rank + c] = Li[(int64_t)a * T + c];
+            S[rank + a] = prop[acc[a]];
+        }
+        rank += n;
+        round += 1;
+    }
+    free(prop); free(u); free(ua); free(H); free(Li); free(acc); free(Y); free(Mm);
+    *rank_out = rank;
+    if (rounds_out) *rounds_out = round;
+    return ORC_OK;
+}
+
 /* Cholesky with the given pivot order (the deterministic recursion of
  * Algorithm 6 with s_i fixed): F is N x k row-major (ld = k); d receives
  * diag(A - F F^*).  A pivot whose residual is <= 0 adds a zero column.
@@ -619,6 +739,16 @@ int orc_rpc_block(const float* X, int d, int kind, double sigma, const double* A
     if (rc) return rc;
     return rpc_block_impl(&M, k, b, max_rounds, seed, inst, F, S, dres, rank, rounds,
                           round_sizes, round_sizes_cap);
+}
+
+int orc_rpc_lowmem(const float* X, int d, int kind, double sigma, const double* A, int64_t N,
+                   int64_t k, int32_t T, int64_t max_rounds, uint64_t seed, uint32_t inst,
+                   double* L, int64_t* S, double* dres, int64_t* rank, int64_t* rounds)
+{
+    orc_matrix M;
+    int rc = make_matrix(&M, X, d, kind, sigma, A, N);
+    if (rc) return rc;
+    return rpc_lowmem_impl(&M, k, T, max_rounds, seed, inst, L, S, dres, rank, rounds);
 }
 
 int orc_fixed_pivot_factor(const float* X, int d, int kind, double sigma, const double* A,

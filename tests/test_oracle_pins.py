@@ -377,6 +377,41 @@ def test_block_rpc_exact_rank_and_semidefinite_chol():
     assert np.allclose(o["F"] @ o["F"].T, D, rtol=0, atol=1e-15)
 
 
+# ---------------------------------------------------------------- Algorithm 3
+
+
+@pytest.mark.parametrize("T", [1, 6, 16])
+def test_lowmem_meets_algorithm_2(T):
+    # Algorithm 3 draws the same pivots as Algorithm 2 and keeps L = F(S,:),
+    # the Cholesky factor of A(S,S) (Sec. 2.4)
+    X = np.random.default_rng(22).standard_normal((90, 3)).astype(np.float32)
+    A = oracle.kernel_matrix(X, "matern52", 1.5)
+    k, seed = 40, 8
+    lo = oracle.rpc_lowmem(k, T, seed, X=X, kernel="matern52", sigma=1.5)
+    ac = oracle.rpc_accel(k, T, seed, X=X, kernel="matern52", sigma=1.5)
+    assert lo["rank"] == ac["rank"] == k and lo["rounds"] == ac["rounds"]
+    assert list(lo["S"]) == list(ac["S"])
+    L, S = lo["L"], lo["S"]
+    assert np.max(np.abs(np.triu(L, 1))) == 0.0 and np.all(np.diag(L) > 0)
+    assert np.max(np.abs(L @ L.T - A[np.ix_(S, S)])) <= 1e-12
+    assert np.max(np.abs(L - ac["F"][S, :])) <= 1e-12
+    # the implicit approximation A(:,S) L^{-*} L^{-1} A(S,:) and its diagonal
+    Z = np.linalg.solve(L, A[S, :])
+    assert np.max(np.abs(np.diag(A) - np.sum(Z * Z, axis=0) - lo["d"])) <= 1e-12
+    assert np.max(np.abs(lo["d"] - ac["d"])) <= 1e-12
+
+
+def test_lowmem_exhaustion_and_k_equals_N():
+    X, A = gauss_matrix(12, 3, 0.6, 23)
+    lo = oracle.rpc_lowmem(12, 5, 3, A=A)
+    assert lo["rank"] == 12 and sorted(lo["S"]) == list(range(12))
+    S = lo["S"]
+    assert np.linalg.norm(lo["L"] @ lo["L"].T - A[np.ix_(S, S)]) <= 1e-12 * np.linalg.norm(A)
+    D = np.diag([4.0, 0.0, 1.0, 0.0, 0.0])
+    lo = oracle.rpc_lowmem(4, 3, 1, A=D)
+    assert lo["rank"] == 2 and sorted(lo["S"]) == [0, 2]
+
+
 def test_zero_weight_stop_returns_lower_rank():
     # Exact exhaustion (Sec. 2.1, sum u = 0): a diagonal matrix whose pivots
     # eliminate exactly in FP64 leaves a zero residual after two pivots.
