@@ -231,6 +231,44 @@ rpchol_status rpchol_trace_error_noalloc(const void* F_dev, int32_t F_dtype, int
  * holds the context must be destroyed first.                              */
 void rpchol_destroy(rpchol_ctx* ctx);
 
+/* ---------------------------------------------------------- low memory
+ * Algorithm 3 (arXiv 2410.03969, Sec. 2.4): accelerated RPCholesky that
+ * keeps no N x k factor.  The context holds X, the residual diagonal, the
+ * pivots S and the Cholesky factor L of A(S,S) (k_max x k_max, FP64, twice:
+ * row- and column-major), and regenerates kernel entries A(R,S) as the
+ * rounds need them: O(N d + k_max^2) device memory, O(N k^2 / T) kernel
+ * evaluations.  It draws the same pivots as rpchol_run in FP64 mode (same
+ * random stream); the implicit approximation is
+ * A(:,S) L^{-*} L^{-1} A(S,:).  FP64 throughout, CUDA cores.
+ * Limits: 1 <= k_max <= min(N, 16384), 1 <= T_max <= 256, d <= 4096.     */
+typedef struct rpchol_lowmem rpchol_lowmem;
+
+/* X: N x d row-major host or device memory (F32 or F64 by x_dtype; copied
+ * to the device, F64 rounded once to F32 as in rpchol_create).  stream:
+ * cudaStream_t (NULL = legacy default) used for every call.
+ * Errors: EINVAL, ENOMEM, ECUDA.                                          */
+rpchol_status rpchol_lowmem_create(int32_t kind, double sigma, const void* X, int64_t N,
+                                   int32_t d, int32_t x_dtype, int64_t k_max, int32_t T_max,
+                                   void* stream, rpchol_lowmem** out);
+
+/* Algorithm 3 to rank k with T proposals per round.  Synchronous (the host
+ * reads the done flag every 8 rounds).  Errors: EINVAL (k, T out of
+ * range), ENUMERIC, ETIMEOUT (round limit 4k + 64), ECUDA.                 */
+rpchol_status rpchol_lowmem_run(rpchol_lowmem* ctx, int64_t k, int32_t T, uint64_t seed);
+
+/* Copy out the last run: L_out (rank x rank, row-major, leading dimension
+ * ld_out >= rank, lower triangular with zeros above the diagonal),
+ * pivots_out (rank), d_out (N: the residual diagonal diag(A - Ahat),
+ * clamped at 0), rank and rounds.  Any pointer may be NULL.  Host or
+ * device destinations.  Errors: EINVAL (ld_out < rank), ECUDA, and the
+ * run's own status.                                                       */
+rpchol_status rpchol_lowmem_copy(rpchol_lowmem* ctx, double* L_out, int64_t ld_out,
+                                 int64_t* pivots_out, double* d_out, int64_t* rank,
+                                 int64_t* rounds);
+
+/* Release the context (NULL accepted).                                    */
+rpchol_status rpchol_lowmem_destroy(rpchol_lowmem* ctx);
+
 /* ---------------------------------------------------------------- batches
  * Many independent factorisations (Algorithm 2 each, arXiv 2410.03969 §3)
  * in one launch: the batch records one CUDA graph in which every context

@@ -82,6 +82,17 @@ _SIGNATURES = [
                                                   ctypes.c_int64, ctypes.c_int64,
                                                   ctypes.c_int64, ctypes.c_void_p,
                                                   ctypes.c_void_p]),
+    ("rpchol_lowmem_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    ("rpchol_lowmem_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_uint64]),
+    ("rpchol_lowmem_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    ("rpchol_lowmem_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("rpchol_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_void_p)]),
@@ -293,6 +304,60 @@ class Factorizer:
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().rpchol_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class LowMemFactorizer:
+    """Algorithm 3 (low-memory accelerated RPCholesky, FP64): keeps the pivots
+    and the Cholesky factor L of A(S,S), never an N x k factor."""
+
+    def __init__(self, X, kernel: str, sigma: float, k_max: int, T_max: int = 256, stream=None):
+        Xn = np.ascontiguousarray(X)
+        if Xn.dtype not in (np.float32, np.float64):
+            Xn = Xn.astype(np.float32)
+        self.N, self.d = int(Xn.shape[0]), int(Xn.shape[1])
+        self._ctx = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        _check(lib().rpchol_lowmem_create(KERNELS[kernel], float(sigma),
+                                          ctypes.c_void_p(Xn.ctypes.data), self.N, self.d,
+                                          0 if Xn.dtype == np.float32 else 1, int(k_max),
+                                          int(T_max), st, ctypes.byref(self._ctx)),
+               "rpchol_lowmem_create")
+
+    def run(self, k: int, T: int, seed: int):
+        _check(lib().rpchol_lowmem_run(self._ctx, int(k), int(T), int(seed) & (2**64 - 1)),
+               "rpchol_lowmem_run")
+        return self
+
+    def copy(self):
+        """Host copies: L (rank x rank, lower triangular), S, d, rank, rounds."""
+        rank, rounds = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().rpchol_lowmem_copy(self._ctx, None, 0, None, None, ctypes.byref(rank),
+                                        ctypes.byref(rounds)), "rpchol_lowmem_copy")
+        r = rank.value
+        L = np.zeros((max(r, 1), max(r, 1)))
+        S = np.zeros(max(r, 1), dtype=np.int64)
+        dres = np.zeros(self.N)
+        _check(lib().rpchol_lowmem_copy(self._ctx, L.ctypes.data, max(r, 1), S.ctypes.data,
+                                        dres.ctypes.data, ctypes.byref(rank),
+                                        ctypes.byref(rounds)), "rpchol_lowmem_copy")
+        return {"L": L[:r, :r], "S": S[:r], "d": dres, "rank": r, "rounds": rounds.value}
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().rpchol_lowmem_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):

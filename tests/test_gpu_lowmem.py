@@ -1,0 +1,121 @@
+"""Low-memory accelerated RPCholesky (Algorithm 3) on the GPU against the
+FP64 oracle.
+
+The pivot sequences must be identical (same Philox stream as Algorithm 2); a
+divergence is tolerated only at a near-tie of the proposal map (running sum
+within 1e-12 W of U W).  L must agree to 1e-10 relative Frobenius error and d
+to 1e-12.  The GPU's L must also equal F(S,:) of the GPU's own FP64
+Algorithm 2 run, and the context must not hold an N x k factor.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+L_TOL = 1e-10
+D_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2410_03969_gb300 as rp
+    rp.lib()
+    return rp
+
+
+def near_tie_at_divergence(X, kernel, sigma, T, seed, S_gpu, S_orc):
+    p = next(i for i in range(min(len(S_gpu), len(S_orc))) if S_gpu[i] != S_orc[i])
+    full = oracle.rpc_accel(len(S_orc), T, seed, X=X, kernel=kernel, sigma=sigma)
+    sizes = full["round_sizes"]
+    rnd = int(np.searchsorted(np.cumsum(sizes), p, side="right"))
+    d = (oracle.rpc_accel(int(np.sum(sizes[:rnd])), T, seed, X=X, kernel=kernel, sigma=sigma,
+                          max_rounds=rnd)["d"] if rnd > 0 else np.ones(X.shape[0]))
+    C = np.cumsum(d)
+    W = float(np.sum(d))
+    for j in range(T):
+        up, _ = oracle.uniform_pair(seed, j, rnd)
+        if np.min(np.abs(C - up * W)) <= 1e-12 * W:
+            return True
+    return False
+
+
+CASES = [
+    # N, d, kernel, sigma, k, T, seed
+    (2000, 8, "gaussian", 3.0, 200, 20, 0),
+    (1200, 5, "matern52", 2.5, 180, 64, 1),     # ragged tiles, several 32-blocks of L
+    (900, 5, "laplace_l1", 5.0, 70, 24, 2),
+    (1000, 4, "laplace_l2", 1.2, 90, 1, 3),     # T = 1
+    (129, 6, "matern32", 1.0, 129, 40, 4),      # k = N
+    (3000, 3, "laplace_l2", 1.0, 300, 128, 5),  # rank past 256: more than 8 blocks of 32
+]
+
+
+@pytest.mark.parametrize("N,d,kernel,sigma,k,T,seed", CASES)
+def test_lowmem_matches_oracle(rp, N, d, kernel, sigma, k, T, seed):
+    X = workloads.gaussian_cloud(N, d, seed + 30)
+    with rp.LowMemFactorizer(X, kernel, sigma, k_max=k, T_max=T) as f:
+        g = f.run(k, T, seed).copy()
+    o = oracle.rpc_lowmem(k, T, seed, X=X, kernel=kernel, sigma=sigma)
+    if g["rank"] != o["rank"] or not np.array_equal(g["S"], o["S"]):
+        assert near_tie_at_divergence(X, kernel, sigma, T, seed, g["S"], o["S"]), \
+            "pivot divergence outside the margin"
+        return
+    assert g["rounds"] == o["rounds"]
+    err = np.linalg.norm(g["L"] - o["L"]) / np.linalg.norm(o["L"])
+    assert err <= L_TOL, err
+    assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
+    assert np.all(np.triu(g["L"], 1) == 0.0)
+
+
+def test_lowmem_equals_gpu_algorithm_2(rp):
+    X = workloads.gaussian_cloud(2500, 6, 40)
+    k, T, seed = 240, 48, 6
+    with rp.LowMemFactorizer(X, "matern52", 2.0, k_max=k, T_max=T) as f:
+        lo = f.run(k, T, seed).copy()
+    with rp.Factorizer(X, "matern52", 2.0, k_max=k, T_max=T, precision="fp64") as f:
+        f.run(k, T, seed).sync()
+        ac = f.copy_factor()
+    assert np.array_equal(lo["S"], ac["S"])
+    FS = ac["F"][ac["S"], :]
+    assert np.linalg.norm(lo["L"] - FS) <= 1e-10 * np.linalg.norm(FS)
+    assert np.max(np.abs(lo["d"] - ac["d"])) <= 1e-12
+
+
+def test_lowmem_reruns_and_shorter_runs(rp):
+    # a second, shorter run on the same context overwrites the first
+    X = workloads.gaussian_cloud(1500, 5, 41)
+    with rp.LowMemFactorizer(X, "gaussian", 2.0, k_max=150, T_max=32) as f:
+        a = f.run(150, 32, 7).copy()
+        b = f.run(60, 32, 7).copy()
+        c = f.run(150, 32, 7).copy()
+    assert b["rank"] == 60 and np.array_equal(b["S"], a["S"][:60])
+    assert np.array_equal(b["L"], a["L"][:60, :60])
+    assert np.array_equal(c["L"], a["L"]) and np.array_equal(c["d"], a["d"])
+
+
+def test_lowmem_holds_no_factor(rp):
+    import torch
+    N, d, k = 1_000_000, 16, 4096
+    X = workloads.gaussian_cloud(N, d, 42)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with rp.LowMemFactorizer(X, "gaussian", 4.0, k_max=k, T_max=128) as f:
+        used = free0 - torch.cuda.mem_get_info()[0]
+        # X (N x 32 floats) + two k x k FP64 copies of L + O(N) vectors,
+        # against 32 GB for an FP64 N x k factor
+        assert used < 1.0e9, used
+        g = f.run(384, 128, 8).copy()
+    assert g["rank"] == 384 and len(set(g["S"].tolist())) == 384
+    S = g["S"]
+    # sampled rows of the residual diagonal against the implicit approximation
+    rows = np.random.default_rng(0).choice(N, 64, replace=False)
+    K_RS = oracle.kernel_matrix(X, "gaussian", 4.0, rows=rows, cols=S)
+    Z = np.linalg.solve(g["L"], K_RS.T)
+    d_exact = np.maximum(1.0 - np.sum(Z * Z, axis=0), 0.0)
+    assert np.max(np.abs(d_exact - g["d"][rows])) <= 1e-10
