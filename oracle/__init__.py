@@ -87,6 +87,10 @@ def _load():
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                       ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, _f64p,
                                       _i64p, _f64p, _i64p, _i64p, _i32p, ctypes.c_int64]
+        lib.orc_rpqr_accel.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                       ctypes.c_uint32, _f64p, _f64p, _i64p, _f64p, _i64p,
+                                       _i64p]
         lib.orc_rpc_lowmem.argtypes = [_f32p, ctypes.c_int, ctypes.c_int, ctypes.c_double, _f64p,
                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, _f64p,
@@ -251,6 +255,28 @@ def rpc_block(k, b, seed, X=None, kernel="gaussian", sigma=1.0, A=None, inst=0, 
     nr = rounds.value
     return {"F": F[:, :r].copy(), "S": S[:r].copy(), "d": dres, "rank": r, "rounds": nr,
             "round_sizes": sizes[:min(nr, cap)].copy()}
+
+
+def rpqr_accel(B, k, T, seed, inst=0, max_rounds=0):
+    """Algorithm 5 (accelerated randomly pivoted QR) of the dense M x N matrix B.
+    Returns dict(Q (M x rank, orthonormal columns), F (N x rank, F = B^* Q), S, u
+    (residual squared column norms), rank, rounds)."""
+    lib = _load()
+    B = np.asarray(B, dtype=np.float64)
+    M, N = B.shape
+    Bc = np.ascontiguousarray(B.T)  # column j of B contiguous
+    Q = np.zeros((max(k, 1), M))
+    F = np.zeros((N, max(k, 1)))
+    S = np.full(max(k, 1), -1, dtype=np.int64)
+    u = np.zeros(N)
+    rank = ctypes.c_int64()
+    rounds = ctypes.c_int64()
+    _check(lib.orc_rpqr_accel(_p(Bc, _f64p), M, N, k, T, max_rounds, seed, inst, _p(Q, _f64p),
+                              _p(F, _f64p), _p(S, _i64p), _p(u, _f64p), ctypes.byref(rank),
+                              ctypes.byref(rounds)), "rpqr_accel")
+    r = rank.value
+    return {"Q": Q[:r].T.copy(), "F": F[:, :r].copy(), "S": S[:r].copy(), "u": u, "rank": r,
+            "rounds": rounds.value}
 
 
 def rpc_lowmem(k, T, seed, X=None, kernel="gaussian", sigma=1.0, A=None, inst=0, max_rounds=0):

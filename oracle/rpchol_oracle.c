@@ -27,6 +27,8 @@
  *   - orc_rpc_plain: simple RPCholesky, Algorithm 6 (appendix).
  *   - orc_rpc_accel: accelerated RPCholesky, Algorithm 2, calling Algorithm 1.
  *   - orc_rpc_block: block RPCholesky, Algorithm 7 (appendix).
+ *   - orc_rpqr_accel: accelerated randomly pivoted QR, Algorithm 5
+ *     (appendix), on a dense rectangular matrix.
  *   - orc_rpc_lowmem: the low-memory form of Algorithm 2, Algorithm 3
  *     (Sec. 2.4): pivots and the k x k Cholesky factor of A(S,S) only.
  *   - orc_fixed_pivot_factor: Cholesky with a given pivot order; it gives the
@@ -646,6 +648,142 @@ static int rpc_lowmem_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t ma
     *rank_out = rank;
     if (rounds_out) *rounds_out = round;
     return ORC_OK;
+}
+
+/* Algorithm 5, accelerated randomly pivoted QR of a dense B (M x N,
+ * column-major: column j at B + j*M).  u starts at the squared column norms.
+ * Per round: the T draws of Algorithm 2 (same Philox blocks; u_i = u[s'_i]),
+ * C = B(:,S') - Q F(S',:)^*, Algorithm 1 on C^* C (its L discarded),
+ * Q_perp = C(:, acc) (= B(:,S_i) - Q F(S_i,:)^*), one more Gram-Schmidt pass
+ * Q_perp -= Q (Q^* Q_perp), Orth = the Q factor of the thin QR with positive
+ * diagonal, formed by classical Gram-Schmidt applied twice column by column;
+ * Q <- [Q Q_perp], G = B^* Q_perp, F <- [F G], u <- max(u - rowsumsq(G), 0).
+ * Q: M x k column-major (ld M); F: N x k row-major (ld k).                 */
+static int rpqr_accel_impl(const double* B, int64_t M, int64_t N, int64_t k, int32_t T,
+                           int64_t max_rounds, uint64_t seed, uint32_t inst, double* Q,
+                           double* F, int64_t* S, double* u, int64_t* rank_out,
+                           int64_t* rounds_out)
+{
+    if (k < 0 || k > N || k > M || T < 1 || M < 1) return ORC_EINVAL;
+    const int64_t kk = k > 0 ? k : 1;
+    memset(Q, 0, sizeof(double) * (size_t)M * (size_t)kk);
+    memset(F, 0, sizeof(double) * (size_t)N * (size_t)kk);
+    for (int64_t j = 0; j < N; ++j) {
+        double t = 0.0;
+        for (int64_t i = 0; i < M; ++i) t += B[j * M + i] * B[j * M + i];
+        u[j] = t;
+    }
+    int64_t* prop = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
+    double* up = (double*)malloc(sizeof(double) * (size_t)T);
+    double* ua = (double*)malloc(sizeof(double) * (size_t)T);
+    double* C = (double*)malloc(sizeof(double) * (size_t)M * T);
+    double* H = (double*)malloc(sizeof(double) * (size_t)T * T);
+    double* L = (double*)malloc(sizeof(double) * (size_t)T * T);
+    int32_t* acc = (int32_t*)malloc(sizeof(int32_t) * (size_t)T);
+    double* w = (double*)malloc(sizeof(double) * (size_t)(kk + T));
+    if (!prop || !up || !ua || !C || !H || !L || !acc || !w) {
+        free(prop); free(up); free(ua); free(C); free(H); free(L); free(acc); free(w);
+        return ORC_ENOMEM;
+    }
+    int64_t rank = 0, round = 0;
+    while (rank < k && (max_rounds <= 0 || round < max_rounds)) {
+        double W = orc_weight_total(u, N);
+        if (!(W > 0.0)) break;
+        for (int32_t j = 0; j < T; ++j) {
+            double Up, Ua;
+            orc_uniform_pair(seed, (uint32_t)j, (uint32_t)round, inst, &Up, &Ua);
+            prop[j] = orc_sample(u, N, W, Up);
+            up[j] = u[prop[j]];
+            ua[j] = Ua;
+        }
+        /* C = B(:,S') - Q F(S',:)^* */
+        for (int32_t a = 0; a < T; ++a)
+            for (int64_t i = 0; i < M; ++i) {
+                double v = B[prop[a] * M + i];
+                for (int64_t m = 0; m < rank; ++m) v -= Q[m * M + i] * F[prop[a] * kk + m];
+                C[(int64_t)a * M + i] = v;
+            }
+        for (int32_t a = 0; a < T; ++a)
+            for (int32_t c = 0; c < T; ++c) {
+                double h = 0.0;
+                for (int64_t i = 0; i < M; ++i) h += C[(int64_t)a * M + i] * C[(int64_t)c * M + i];
+                H[(int64_t)a * T + c] = h;
+            }
+        int32_t n = 0;
+        int rc = orc_reject_chol(H, T, up, ua, (int32_t)(k - rank), acc, L, &n);
+        if (rc != ORC_OK) {
+            free(prop); free(up); free(ua); free(C); free(H); free(L); free(acc); free(w);
+            return rc;
+        }
+        /* Q_perp = C(:,acc) into Q(:, rank:rank+n), re-orthogonalised against Q */
+        for (int32_t a = 0; a < n; ++a) {
+            double* q = Q + (rank + a) * M;
+            memcpy(q, C + (int64_t)acc[a] * M, sizeof(double) * (size_t)M);
+            S[rank + a] = prop[acc[a]];
+        }
+        for (int32_t a = 0; a < n; ++a) {
+            double* q = Q + (rank + a) * M;
+            for (int64_t m = 0; m < rank; ++m) {
+                double t = 0.0;
+                for (int64_t i = 0; i < M; ++i) t += Q[m * M + i] * q[i];
+                w[m] = t;
+            }
+            for (int64_t i = 0; i < M; ++i) {
+                double v = q[i];
+                for (int64_t m = 0; m < rank; ++m) v -= Q[m * M + i] * w[m];
+                q[i] = v;
+            }
+        }
+        /* Orth: column a against columns rank..rank+a-1, twice, then normalised */
+        for (int32_t a = 0; a < n; ++a) {
+            double* q = Q + (rank + a) * M;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int32_t c = 0; c < a; ++c) {
+                    const double* qc = Q + (rank + c) * M;
+                    double t = 0.0;
+                    for (int64_t i = 0; i < M; ++i) t += qc[i] * q[i];
+                    w[c] = t;
+                }
+                for (int64_t i = 0; i < M; ++i) {
+                    double v = q[i];
+                    for (int32_t c = 0; c < a; ++c) v -= Q[(rank + c) * M + i] * w[c];
+                    q[i] = v;
+                }
+            }
+            double nrm = 0.0;
+            for (int64_t i = 0; i < M; ++i) nrm += q[i] * q[i];
+            nrm = sqrt(nrm);
+            for (int64_t i = 0; i < M; ++i) q[i] /= nrm;
+        }
+        /* G = B^* Q_perp; F <- [F G]; u update */
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
+        for (int64_t j = 0; j < N; ++j) {
+            double rsq = 0.0;
+            for (int32_t a = 0; a < n; ++a) {
+                const double* q = Q + (rank + a) * M;
+                double g = 0.0;
+                for (int64_t i = 0; i < M; ++i) g += B[j * M + i] * q[i];
+                F[j * kk + rank + a] = g;
+                rsq += g * g;
+            }
+            double v = u[j] - rsq;
+            u[j] = v > 0.0 ? v : 0.0;
+        }
+        rank += n;
+        round += 1;
+    }
+    free(prop); free(up); free(ua); free(C); free(H); free(L); free(acc); free(w);
+    *rank_out = rank;
+    if (rounds_out) *rounds_out = round;
+    return ORC_OK;
+}
+
+int orc_rpqr_accel(const double* B, int64_t M, int64_t N, int64_t k, int32_t T,
+                   int64_t max_rounds, uint64_t seed, uint32_t inst, double* Q, double* F,
+                   int64_t* S, double* u, int64_t* rank, int64_t* rounds)
+{
+    if (!B || !Q || !F || !S || !u || !rank) return ORC_EINVAL;
+    return rpqr_accel_impl(B, M, N, k, T, max_rounds, seed, inst, Q, F, S, u, rank, rounds);
 }
 
 /* Cholesky with the given pivot order (the deterministic recursion of

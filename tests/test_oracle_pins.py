@@ -412,6 +412,42 @@ def test_lowmem_exhaustion_and_k_equals_N():
     assert lo["rank"] == 2 and sorted(lo["S"]) == [0, 2]
 
 
+# ---------------------------------------------------------------- Algorithm 5
+
+
+@pytest.mark.parametrize("T", [1, 5, 12])
+def test_rpqr_meets_rpcholesky_on_the_gram_matrix(T):
+    # QR-Cholesky correspondence (appendix proposition): with the same pivots,
+    # RPQR of B gives the Cholesky factor of A = B^* B; the same random stream
+    # then draws the same pivots
+    rng = np.random.default_rng(24)
+    M, N = 40, 70
+    B = rng.standard_normal((M, 6)) @ rng.standard_normal((6, N)) + 0.05 * rng.standard_normal((M, N))
+    A = B.T @ B
+    k, seed = 25, 5
+    qr = oracle.rpqr_accel(B, k, T, seed)
+    ch = oracle.rpc_accel(k, T, seed, A=A)
+    assert qr["rank"] == ch["rank"] == k and list(qr["S"]) == list(ch["S"])
+    assert np.linalg.norm(qr["F"] - ch["F"]) <= 1e-10 * np.linalg.norm(ch["F"])
+    assert np.max(np.abs(qr["u"] - ch["d"])) <= 1e-10 * np.max(np.diag(A))
+    # Q orthonormal, F = B^* Q, u = squared column norms of (I - QQ^*) B
+    Q = qr["Q"]
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) <= 1e-12
+    assert np.max(np.abs(qr["F"] - B.T @ Q)) <= 1e-12 * np.max(np.abs(B))
+    R = B - Q @ (Q.T @ B)
+    assert np.max(np.abs(np.sum(R * R, axis=0) - qr["u"])) <= 1e-10 * np.max(np.diag(A))
+    # the pivot columns are reproduced exactly
+    S = qr["S"]
+    assert np.max(np.abs(R[:, S])) <= 1e-10 * np.max(np.abs(B))
+
+
+def test_rpqr_full_rank_exhaustion():
+    B = np.random.default_rng(25).standard_normal((5, 9))
+    qr = oracle.rpqr_accel(B, 5, 4, 1)
+    assert qr["rank"] == 5
+    assert np.linalg.norm(qr["Q"] @ qr["F"].T - B) <= 1e-12 * np.linalg.norm(B)
+
+
 def test_zero_weight_stop_returns_lower_rank():
     # Exact exhaustion (Sec. 2.1, sum u = 0): a diagonal matrix whose pivots
     # eliminate exactly in FP64 leaves a zero residual after two pivots.
