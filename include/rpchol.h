@@ -269,6 +269,42 @@ rpchol_status rpchol_lowmem_copy(rpchol_lowmem* ctx, double* L_out, int64_t ld_o
 /* Release the context (NULL accepted).                                    */
 rpchol_status rpchol_lowmem_destroy(rpchol_lowmem* ctx);
 
+/* --------------------------------------------------- randomly pivoted QR
+ * Algorithm 5 (arXiv 2410.03969, appendix): accelerated randomly pivoted
+ * QR of a dense M x N matrix B, FP64 on CUDA cores.  Each round draws T
+ * columns from the residual squared column norms u, accepts a subset by
+ * Algorithm 1 on C^* C with C = B(:,S') - Q F(S',:)^*, orthonormalises the
+ * accepted residual columns (a second Gram-Schmidt pass against Q, then the
+ * thin-QR factor with positive diagonal by Cholesky QR twice) and appends
+ * them to Q, appends G = B^* Q_perp to F, and subtracts the squared row
+ * norms of G from u.  B ~ Q F^*.  Same random stream as rpchol_run, so that
+ * it draws the pivots rpchol_run draws on A = B^* B.                      */
+typedef struct rpchol_rpqr rpchol_rpqr;
+
+/* B: column-major M x N, leading dimension ldb >= M, host or device; copied.
+ * Device memory: N M + (k_max + 256) M + N k_max doubles and O(N) vectors.
+ * 1 <= k_max <= min(M, N), 1 <= T_max <= 256.  stream as in
+ * rpchol_lowmem_create.  Errors: EINVAL, ENOMEM, ECUDA.                   */
+rpchol_status rpchol_rpqr_create(const double* B, int64_t M, int64_t N, int64_t ldb,
+                                 int64_t k_max, int32_t T_max, void* stream, rpchol_rpqr** out);
+
+/* Algorithm 5 to rank k (the round that would pass k stops at k), T
+ * proposals per round.  Synchronous (the host reads the accepted count
+ * each round).  Errors: EINVAL, ENUMERIC, ETIMEOUT (round limit), ECUDA.   */
+rpchol_status rpchol_rpqr_run(rpchol_rpqr* ctx, int64_t k, int32_t T, uint64_t seed);
+
+/* Copy out the last run: Q_out (M x rank column-major, ldq >= M, orthonormal
+ * columns), F_out (N x rank row-major, ldf >= rank, F = B^* Q), pivots_out
+ * (rank), u_out (N residual squared column norms), rank, rounds.  Any
+ * pointer may be NULL; host or device destinations.  Errors: EINVAL
+ * (leading dimension too small), ECUDA, and the run's own status.         */
+rpchol_status rpchol_rpqr_copy(rpchol_rpqr* ctx, double* Q_out, int64_t ldq, double* F_out,
+                               int64_t ldf, int64_t* pivots_out, double* u_out, int64_t* rank,
+                               int64_t* rounds);
+
+/* Release the context (NULL accepted).                                    */
+rpchol_status rpchol_rpqr_destroy(rpchol_rpqr* ctx);
+
 /* ---------------------------------------------------------------- batches
  * Many independent factorisations (Algorithm 2 each, arXiv 2410.03969 §3)
  * in one launch: the batch records one CUDA graph in which every context

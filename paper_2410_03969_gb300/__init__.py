@@ -93,6 +93,16 @@ _SIGNATURES = [
                                           ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]),
     ("rpchol_lowmem_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("rpchol_rpqr_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("rpchol_rpqr_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_uint64]),
+    ("rpchol_rpqr_copy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    ("rpchol_rpqr_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("rpchol_batch_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                                            ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_void_p)]),
@@ -358,6 +368,59 @@ class LowMemFactorizer:
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().rpchol_lowmem_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class RPQR:
+    """Algorithm 5 (accelerated randomly pivoted QR, FP64) of a dense M x N
+    matrix B: B ~ Q F^* with orthonormal Q (M x k) and F = B^* Q (N x k)."""
+
+    def __init__(self, B, k_max: int, T_max: int = 256, stream=None):
+        Bf = np.asfortranarray(np.asarray(B, dtype=np.float64))
+        self.M, self.N = int(Bf.shape[0]), int(Bf.shape[1])
+        self._ctx = ctypes.c_void_p()
+        st = stream if stream is not None else _current_stream()
+        _check(lib().rpchol_rpqr_create(ctypes.c_void_p(Bf.ctypes.data), self.M, self.N, self.M,
+                                        int(k_max), int(T_max), st, ctypes.byref(self._ctx)),
+               "rpchol_rpqr_create")
+
+    def run(self, k: int, T: int, seed: int):
+        _check(lib().rpchol_rpqr_run(self._ctx, int(k), int(T), int(seed) & (2**64 - 1)),
+               "rpchol_rpqr_run")
+        return self
+
+    def copy(self):
+        """Host copies: Q (M x rank), F (N x rank), S, u, rank, rounds."""
+        rank, rounds = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().rpchol_rpqr_copy(self._ctx, None, self.M, None, 1, None, None,
+                                      ctypes.byref(rank), ctypes.byref(rounds)), "rpchol_rpqr_copy")
+        r = rank.value
+        Qt = np.zeros((max(r, 1), self.M))  # column-major Q: one row per column
+        F = np.zeros((self.N, max(r, 1)))
+        S = np.zeros(max(r, 1), dtype=np.int64)
+        u = np.zeros(self.N)
+        _check(lib().rpchol_rpqr_copy(self._ctx, Qt.ctypes.data, self.M, F.ctypes.data,
+                                      max(r, 1), S.ctypes.data, u.ctypes.data,
+                                      ctypes.byref(rank), ctypes.byref(rounds)),
+               "rpchol_rpqr_copy")
+        return {"Q": Qt[:r].T.copy(), "F": F[:, :r].copy(), "S": S[:r], "u": u, "rank": r,
+                "rounds": rounds.value}
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().rpchol_rpqr_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):
