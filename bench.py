@@ -638,6 +638,30 @@ def colgen_measure(args):
     return 0
 
 
+def profile_case(args):
+    """One run of Algorithm 3 or Algorithm 5 on a fixed case, for ncu captures
+    (no bench line): lowmem = the bench workload to rank k; rpqr = a dense
+    2000 x 20000 matrix to rank 500 with T = 128."""
+    import torch
+    import paper_2410_03969_gb300 as rp
+    rp.lib()
+    if args.profile_case == "lowmem":
+        prob = _problem(args)
+        with rp.LowMemFactorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k,
+                                 T_max=prob.T) as lm:
+            out = lm.run(prob.k, prob.T, 1).copy()
+        print(json.dumps({"case": "lowmem", "rank": out["rank"], "rounds": out["rounds"]}))
+    else:
+        rng = np.random.default_rng(5)
+        B = (rng.standard_normal((2000, 400)) @ rng.standard_normal((400, 20000))
+             + 0.01 * rng.standard_normal((2000, 20000)))
+        with rp.RPQR(B, k_max=500, T_max=128) as qr:
+            out = qr.run(500, 128, 1).copy()
+        print(json.dumps({"case": "rpqr", "rank": out["rank"], "rounds": out["rounds"]}))
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -663,7 +687,11 @@ def main():
                     help="FP64 FMA peak (TFLOP/s) measured on GB300 by an FMA-loop probe")
     ap.add_argument("--colgen", action="store_true",
                     help="columns per second against the block size (no bench line)")
+    ap.add_argument("--profile-case", choices=["lowmem", "rpqr"], default=None,
+                    help="one run of Algorithm 3 or 5 for profiling (no bench line)")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
     if args.colgen:
         return colgen_measure(args)
     if args.impl == "reference":

@@ -66,3 +66,38 @@ def test_invalid_arguments_are_rejected_before_any_launch(library):
         assert rc == 1, args
         assert rp.lib().rpchol_last_error()
     assert rp.lib().rpchol_run(None, 1, 1, 0) == 1
+
+
+def test_binding_binds_every_declared_symbol():
+    bound = {n for n, _, _ in rp._SIGNATURES}
+    missing = [n for n in declared_symbols() if n not in bound]
+    assert not missing, missing
+
+
+def test_invalid_arguments_of_the_other_algorithms(library):
+    L = rp.lib()
+    out = ctypes.c_void_p()
+    x = (ctypes.c_float * 64)()
+    xp = ctypes.cast(x, ctypes.c_void_p)
+    # block RPCholesky on no context
+    assert L.rpchol_run_block(None, 1, 1, 0) == 1
+    # low memory: k_max > N, k_max > 16384, T_max > 256, bad kind, bad dtype
+    for kind, sigma, N, d, dt, kmax, tmax in ((0, 1.0, 8, 2, 0, 9, 4),
+                                             (0, 1.0, 20000, 2, 0, 16385, 4),
+                                             (0, 1.0, 8, 2, 0, 4, 257),
+                                             (5, 1.0, 8, 2, 0, 4, 4),
+                                             (0, 1.0, 8, 2, 3, 4, 4)):
+        assert L.rpchol_lowmem_create(kind, sigma, xp, N, d, dt, kmax, tmax, None,
+                                      ctypes.byref(out)) == 1
+        assert not out.value
+    assert L.rpchol_lowmem_run(None, 1, 1, 0) == 1
+    assert L.rpchol_lowmem_copy(None, None, 0, None, None, None, None) == 1
+    assert L.rpchol_lowmem_destroy(None) == 0
+    # RPQR: ldb < M, k_max > min(M, N), T_max > 256
+    b = (ctypes.c_double * 64)()
+    bp = ctypes.cast(b, ctypes.c_void_p)
+    for M, N, ldb, kmax, tmax in ((8, 8, 4, 2, 2), (4, 16, 4, 5, 2), (8, 8, 8, 2, 257)):
+        assert L.rpchol_rpqr_create(bp, M, N, ldb, kmax, tmax, None, ctypes.byref(out)) == 1
+    assert L.rpchol_rpqr_run(None, 1, 1, 0) == 1
+    assert L.rpchol_rpqr_copy(None, None, 0, None, 0, None, None, None, None) == 1
+    assert L.rpchol_rpqr_destroy(None) == 0
