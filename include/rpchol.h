@@ -282,7 +282,8 @@ rpchol_status rpchol_lowmem_destroy(rpchol_lowmem* ctx);
 typedef struct rpchol_rpqr rpchol_rpqr;
 
 /* B: column-major M x N, leading dimension ldb >= M, host or device; copied.
- * Device memory: N M + (k_max + 256) M + N k_max doubles and O(N) vectors.
+ * Device memory: N M + (k_max + 256) M + N k_max doubles, a split-K
+ * workspace of max(4 k_max, 16384) x 256 doubles and O(N) vectors.
  * 1 <= k_max <= min(M, N), 1 <= T_max <= 256.  stream as in
  * rpchol_lowmem_create.  Errors: EINVAL, ENOMEM, ECUDA.                   */
 rpchol_status rpchol_rpqr_create(const double* B, int64_t M, int64_t N, int64_t ldb,

@@ -34,13 +34,19 @@ constexpr int kGM = 64, kGN = 64, kGK = 8;
 // C(i,j) = beta C(i,j) + alpha sum_k A(i,k) B(k,j) for i < m, j < n, k < K;
 // X(r,c) = X[r * xr + c * xc].  Each operand's staging order follows its
 // unit stride (coalesced along it).
+// Split K (gridDim.z > 1): CTA z sums k in [z Kc, (z + 1) Kc) and writes
+// alpha times its partial to P + z m n (dense, row-major); k_splitk_sum adds
+// the partials in z order, so the result does not depend on scheduling.
 __global__ void __launch_bounds__(256)
     k_dgemm(long long m, long long n, long long K, double alpha, const double* __restrict__ A,
             long long ar, long long ac, const double* __restrict__ Bm, long long br,
-            long long bc, double beta, double* C, long long cr, long long cc) {
+            long long bc, double beta, double* C, long long cr, long long cc, long long Kc,
+            double* P) {
   __shared__ double As[kGK][kGM + 1];
   __shared__ double Bs[kGK][kGN + 1];
   const long long i0 = (long long)blockIdx.y * kGM, j0 = (long long)blockIdx.x * kGN;
+  const long long kb = (long long)blockIdx.z * Kc;
+  const long long ke = kb + Kc < K ? kb + Kc : K;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   double acc[4][4];
 #pragma unroll
@@ -48,18 +54,18 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
   const bool a_k_fast = ac == 1, b_k_fast = br == 1;
-  for (long long k0 = 0; k0 < K; k0 += kGK) {
+  for (long long k0 = kb; k0 < ke; k0 += kGK) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int e = tid + 256 * q;
       int r, kk;
       if (a_k_fast) { r = e >> 3; kk = e & 7; } else { r = e & 63; kk = e >> 6; }
       const long long gi = i0 + r, gk = k0 + kk;
-      As[kk][r] = (gi < m && gk < K) ? A[gi * ar + gk * ac] : 0.0;
-      int c, kb;
-      if (b_k_fast) { c = e >> 3; kb = e & 7; } else { c = e & 63; kb = e >> 6; }
-      const long long gj = j0 + c, gkb = k0 + kb;
-      Bs[kb][c] = (gj < n && gkb < K) ? Bm[gkb * br + gj * bc] : 0.0;
+      As[kk][r] = (gi < m && gk < ke) ? A[gi * ar + gk * ac] : 0.0;
+      int c, kq;
+      if (b_k_fast) { c = e >> 3; kq = e & 7; } else { c = e & 63; kq = e >> 6; }
+      const long long gj = j0 + c, gkb = k0 + kq;
+      Bs[kq][c] = (gj < n && gkb < ke) ? Bm[gkb * br + gj * bc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -84,18 +90,65 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < 4; ++j) {
       const long long gj = j0 + tx * 4 + j;
       if (gj >= n) continue;
-      double* p = C + gi * cr + gj * cc;
-      *p = beta == 0.0 ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *p);
+      if (P) {
+        P[((long long)blockIdx.z * m + gi) * n + gj] = alpha * acc[i][j];
+      } else {
+        double* p = C + gi * cr + gj * cc;
+        *p = beta == 0.0 ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *p);
+      }
     }
   }
 }
 
+__global__ void __launch_bounds__(256)
+    k_splitk_sum(long long m, long long n, int splits, const double* __restrict__ P, double beta,
+                 double* C, long long cr, long long cc) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * n) return;
+  const long long i = e / n, j = e % n;
+  double v = 0.0;
+  for (int z = 0; z < splits; ++z) v += P[(long long)z * m * n + e];
+  double* p = C + i * cr + j * cc;
+  *p = beta == 0.0 ? v : fma(beta, *p, v);
+}
+
+// Workspace for split-K partials (doubles), owned by the context.
+struct SplitWs {
+  double* p = nullptr;
+  long long cap = 0;
+  int num_sms = 148;
+};
+
+// C = beta C + alpha A B.  Few output tiles over a long K (the Gram-type
+// products H, Q^* Q_perp, Q_perp^* Q_perp) split K across CTAs so that the
+// grid covers the GPU.
 cudaError_t dgemm(long long m, long long n, long long K, double alpha, const double* A,
                   long long ar, long long ac, const double* B, long long br, long long bc,
-                  double beta, double* C, long long cr, long long cc, cudaStream_t s) {
+                  double beta, double* C, long long cr, long long cc, cudaStream_t s,
+                  const SplitWs* ws = nullptr) {
   if (m <= 0 || n <= 0 || (K <= 0 && beta == 1.0)) return cudaSuccess;
-  const dim3 grid((unsigned)((n + kGN - 1) / kGN), (unsigned)((m + kGM - 1) / kGM));
-  k_dgemm<<<grid, 256, 0, s>>>(m, n, K, alpha, A, ar, ac, B, br, bc, beta, C, cr, cc);
+  const long long tiles = ((n + kGN - 1) / kGN) * ((m + kGM - 1) / kGM);
+  int splits = 1;
+  if (ws && ws->p && K >= 1024 && tiles < ws->num_sms) {
+    long long want = (2LL * ws->num_sms + tiles - 1) / tiles;
+    const long long by_k = K / 256;
+    const long long by_ws = ws->cap / (m * n);
+    if (want > by_k) want = by_k;
+    if (want > by_ws) want = by_ws;
+    if (want > 64) want = 64;
+    if (want > 1) splits = (int)want;
+  }
+  long long Kc = K;
+  if (splits > 1) Kc = (((K + splits - 1) / splits) + kGK - 1) / kGK * kGK;
+  if (splits > 1) splits = (int)((K + Kc - 1) / Kc);
+  const dim3 grid((unsigned)((n + kGN - 1) / kGN), (unsigned)((m + kGM - 1) / kGM),
+                  (unsigned)splits);
+  k_dgemm<<<grid, 256, 0, s>>>(m, n, K, alpha, A, ar, ac, B, br, bc, beta, C, cr, cc,
+                               splits > 1 ? Kc : (K > 0 ? K : 1), splits > 1 ? ws->p : nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  k_splitk_sum<<<(unsigned)((m * n + 255) / 256), 256, 0, s>>>(m, n, splits, ws->p, beta, C, cr,
+                                                              cc);
   return cudaGetLastError();
 }
 
@@ -221,6 +274,7 @@ struct rpchol_rpqr {
   double* Fg = nullptr;   // T_max x ldF
   double* Wm = nullptr;   // k_max x T_max
   double* Gs = nullptr;   // T_max x T_max
+  SplitWs ws;             // split-K partials
   DevState* st_host = nullptr;
   std::vector<void*> owned;
   int has_run = 0;
@@ -335,6 +389,12 @@ rpchol_status rpchol_rpqr_create(const double* B, int64_t M, int64_t N, int64_t 
   QRALLOC(c->Fg, double, (size_t)kTMax * b.ldF);
   QRALLOC(c->Wm, double, (size_t)k_max * kTMax);
   QRALLOC(c->Gs, double, (size_t)kTMax * kTMax);
+  // split-K partials: at least 4 splits of the largest Gram-type product
+  // (k_max x 256), 64 of a 256 x 256 one
+  c->ws.cap = 4 * (long long)k_max * kTMax;
+  if (c->ws.cap < 64LL * kTMax * kTMax) c->ws.cap = 64LL * kTMax * kTMax;
+  QRALLOC(c->ws.p, double, (size_t)c->ws.cap);
+  c->ws.num_sms = b.num_sms;
   double* Fp;
   QRALLOC(Fp, double, (size_t)N * b.ldF);
   b.F = Fp;
@@ -387,7 +447,7 @@ rpchol_status rpchol_rpqr_run(rpchol_rpqr* c, int64_t k, int32_t T, uint64_t see
     // C = B(:,S') - Q F(S',:)^*, stored as rows: Cg(a,i) -= sum_m Fg(a,m) Q(i,m)
     QRCU(dgemm(T, M, rank, -1.0, c->Fg, ldF, 1, c->Qc, M, 1, 1.0, c->Cg, M, 1, s));
     // H = C^* C (ld T)
-    QRCU(dgemm(T, T, M, 1.0, c->Cg, M, 1, c->Cg, 1, M, 0.0, b.H, T, 1, s));
+    QRCU(dgemm(T, T, M, 1.0, c->Cg, M, 1, c->Cg, 1, M, 0.0, b.H, T, 1, s, &c->ws));
     QRCU(launch_reject(b, T, s));
     rpchol_status r = read_st(c);
     if (r != RPCHOL_OK) return r;
@@ -398,11 +458,11 @@ rpchol_status rpchol_rpqr_run(rpchol_rpqr* c, int64_t k, int32_t T, uint64_t see
       QRCU(cudaGetLastError());
       double* Qp = c->Qc + rank * M;
       // second Gram-Schmidt pass against the earlier columns
-      QRCU(dgemm(rank, sa, M, 1.0, c->Qc, M, 1, Qp, 1, M, 0.0, c->Wm, kTMax, 1, s));
+      QRCU(dgemm(rank, sa, M, 1.0, c->Qc, M, 1, Qp, 1, M, 0.0, c->Wm, kTMax, 1, s, &c->ws));
       QRCU(dgemm(sa, M, rank, -1.0, c->Wm, 1, kTMax, c->Qc, M, 1, 1.0, Qp, M, 1, s));
       // Cholesky QR twice: the thin-QR factor with positive diagonal
       for (int pass = 0; pass < 2; ++pass) {
-        QRCU(dgemm(sa, sa, M, 1.0, Qp, M, 1, Qp, 1, M, 0.0, c->Gs, kTMax, 1, s));
+        QRCU(dgemm(sa, sa, M, 1.0, Qp, M, 1, Qp, 1, M, 0.0, c->Gs, kTMax, 1, s, &c->ws));
         k_qr_chol<<<1, 1024, 0, s>>>(b.st, c->Gs, sa, kTMax);
         QRCU(cudaGetLastError());
         k_qr_trsm<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(c->Gs, kTMax, sa, c->Qc, M, rank);
