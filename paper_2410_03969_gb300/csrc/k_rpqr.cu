@@ -359,7 +359,6 @@ rpchol_status rpchol_rpqr_create(const double* B, int64_t M, int64_t N, int64_t 
       nsm = 148;
     b.num_sms = nsm;
   }
-  rpchol_status rs = RPCHOL_OK;
   auto fail = [&](rpchol_status s) {
     qr_release(c);
     delete c;
@@ -413,7 +412,6 @@ rpchol_status rpchol_rpqr_create(const double* B, int64_t M, int64_t N, int64_t 
   QRALLOC(b.red, double, b.nred);
   QRALLOC(b.st, DevState, 1);
 #undef QRALLOC
-  (void)rs;
   e = cudaMemcpy2DAsync(c->Bc, sizeof(double) * M, B, sizeof(double) * ldb, sizeof(double) * M,
                         N, cudaMemcpyDefault, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.F, 0, sizeof(double) * (size_t)N * b.ldF, c->stream);
