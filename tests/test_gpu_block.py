@@ -122,3 +122,27 @@ def test_block_mixed_mode(rp, N, d, kernel, sigma, k, b):
     dd = 1.0 - np.sum(F * F, axis=1)
     assert np.max(np.abs(np.maximum(dd, 0.0) - g["d"])) <= 2e-3
     assert abs(st["trace_error"] - te / N) <= 5e-3 * te / N + 1e-9
+
+
+def test_block_full_size_mixed_sampled_rows(rp):
+    """Block RPCholesky at the benchmarked size (N = 1e5, d = 20, k = 1000,
+    b = 120, mixed precision): sampled rows and pivot rows of F equal the exact
+    Nystrom factor of the GPU's pivots to FP32 accuracy, every pivot is a
+    distinct index, and the trace error is sum(d) / N."""
+    from test_gpu_mixed import _exact_rows, _rows_from_device
+    prob = workloads.mixture20_n1e5(0)
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
+                       precision="mixed") as f:
+        f.run_block(prob.k, prob.T, 0).sync()
+        st = f.stats()
+        g = f.copy_factor(F=False, pivots=True, d=True)
+        assert st["status"] == 0 and st["plain"] == 2 and g["rank"] == prob.k
+        S = g["S"]
+        assert len(set(S.tolist())) == prob.k
+        rng = np.random.default_rng(2)
+        rows = np.concatenate([rng.choice(prob.N, 40, replace=False), S[:4], S[-4:]])
+        Fg = _rows_from_device(f, rows, prob.k)
+    Fr = _exact_rows(prob, S, rows)
+    err = np.linalg.norm(Fg - Fr) / np.linalg.norm(Fr)
+    assert err <= 5e-4, err
+    assert st["trace_error"] == pytest.approx(np.sum(g["d"]) / prob.N, rel=1e-6, abs=1e-12)

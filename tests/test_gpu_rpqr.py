@@ -72,3 +72,28 @@ def test_rpqr_matches_oracle(rp, M, N, r, noise, k, T, seed):
     assert np.max(np.abs(g["u"] - o["u"])) <= 1e-10 * u0
     if k == M:
         assert np.linalg.norm(g["Q"] @ g["F"].T - B) <= 1e-10 * np.linalg.norm(B)
+
+
+def test_rpqr_full_size_properties(rp):
+    """The benchmarked case (dense 2000 x 20000, numerical rank about 400, k =
+    500, T = 128), checked through properties that hold at any size: Q has
+    orthonormal columns, sampled rows of F equal B^* Q, sampled u equal the
+    squared column norms of B - Q Q^* B, the pivots are distinct, and the
+    pivot columns are reproduced."""
+    rng = np.random.default_rng(5)
+    M, N, k, T = 2000, 20000, 500, 128
+    B = rng.standard_normal((M, 400)) @ rng.standard_normal((400, N)) \
+        + 0.01 * rng.standard_normal((M, N))
+    with rp.RPQR(B, k_max=k, T_max=T) as f:
+        g = f.run(k, T, 1).copy()
+    Q, F, S, u = g["Q"], g["F"], g["S"], g["u"]
+    assert g["rank"] == k and len(set(S.tolist())) == k
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) <= 1e-11
+    cols = np.concatenate([rng.choice(N, 64, replace=False), S[:4], S[-4:]])
+    Fx = B[:, cols].T @ Q
+    assert np.max(np.abs(F[cols] - Fx)) <= 1e-10 * np.max(np.abs(Fx))
+    R = B[:, cols] - Q @ Fx.T
+    ux = np.sum(R * R, axis=0)
+    scale = np.max(np.sum(B[:, cols] ** 2, axis=0))
+    assert np.max(np.abs(u[cols] - np.maximum(ux, 0.0))) <= 1e-9 * scale
+    assert np.max(np.abs(R[:, -8:])) <= 1e-9 * np.sqrt(scale)
