@@ -227,6 +227,26 @@ rpchol_status rpchol_trace_error_noalloc(const void* F_dev, int32_t F_dtype, int
                                          int64_t ldF, int64_t rank, double* out_dev,
                                          void* stream);
 
+/* Checkpoints.  rpchol_save writes the state of the last run (run state,
+ * residual diagonal, tile sums, pivots and the rank columns of F in the
+ * stored dtype) to host_buf; with host_buf NULL it only sets *bytes to the
+ * size needed.  Synchronous.  rpchol_restore loads such a buffer into a
+ * context created with the same X, kernel, sigma, N, d and precision and
+ * k_max >= the saved rank (T_max >= the saved T); afterwards
+ * rpchol_factor / rpchol_copy_factor / rpchol_stats describe the saved run.
+ * X itself is not saved.  Errors: EINVAL (no run yet, buffer too small
+ * (*bytes then holds the size needed), foreign or mismatched checkpoint),
+ * ECUDA.                                                                  */
+rpchol_status rpchol_save(rpchol_ctx* ctx, void* host_buf, size_t* bytes);
+rpchol_status rpchol_restore(rpchol_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Continue the last run (or the restored one) from its current rank to rank
+ * k > rank with the same algorithm, block size and random stream: the next
+ * round is the saved round counter, so a resumed run draws what the
+ * original context would have drawn had it been resumed itself.  The run's
+ * status must be OK.  Asynchronous like rpchol_run.  Errors: EINVAL.       */
+rpchol_status rpchol_resume(rpchol_ctx* ctx, int64_t k);
+
 /* Release everything the context owns.  NULL is accepted.  A batch that
  * holds the context must be destroyed first.                              */
 void rpchol_destroy(rpchol_ctx* ctx);

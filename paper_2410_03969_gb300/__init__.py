@@ -78,6 +78,10 @@ _SIGNATURES = [
                                               ctypes.c_void_p]),
     ("rpchol_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RunStats)]),
     ("rpchol_destroy", None, [ctypes.c_void_p]),
+    ("rpchol_save", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_size_t)]),
+    ("rpchol_restore", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("rpchol_resume", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     ("rpchol_trace_error_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                                   ctypes.c_int64, ctypes.c_int64,
                                                   ctypes.c_int64, ctypes.c_void_p,
@@ -248,6 +252,23 @@ class Factorizer:
     def run_block(self, k: int, b: int, seed: int):
         _check(lib().rpchol_run_block(self._ctx, int(k), int(b), int(seed) & (2**64 - 1)),
                "rpchol_run_block")
+        return self
+
+    def save(self) -> bytes:
+        """Checkpoint of the last run (host bytes)."""
+        n = ctypes.c_size_t(0)
+        _check(lib().rpchol_save(self._ctx, None, ctypes.byref(n)), "rpchol_save")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().rpchol_save(self._ctx, buf, ctypes.byref(n)), "rpchol_save")
+        return buf.raw[:n.value]
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().rpchol_restore(self._ctx, buf, len(blob)), "rpchol_restore")
+        return self
+
+    def resume(self, k: int):
+        _check(lib().rpchol_resume(self._ctx, int(k)), "rpchol_resume")
         return self
 
     def sync(self):

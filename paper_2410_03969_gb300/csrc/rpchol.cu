@@ -305,6 +305,8 @@ void clear_prof(rpchol_ctx* c) {
 
 // mode 0: accelerated (Algorithm 2), 1: simple (Algorithm 6), 2: block (Algorithm 7, the
 // accelerated loop body with the acceptance rule switched in the device state)
+rpchol_status run_loop(rpchol_ctx* c, int plain, int T, long long max_rounds);
+
 rpchol_status run_common(rpchol_ctx* c, int mode, long long k, int T, unsigned long long seed) {
   const int plain = mode == 1;
   const long long max_rounds = plain ? 2 * k + 64 : 4 * k + 64;
@@ -312,6 +314,11 @@ rpchol_status run_common(rpchol_ctx* c, int mode, long long k, int T, unsigned l
   CU(launch_reset(c->b, k, T, seed, c->instance, mode, max_rounds, c->stream));
   c->last_plain = plain;
   c->has_run = 1;
+  return run_loop(c, plain, T, max_rounds);
+}
+
+// The round loop of a run whose device state is set (fresh or resumed).
+rpchol_status run_loop(rpchol_ctx* c, int plain, int T, long long max_rounds) {
   c->host_iters = -1;
   if (c->use_graph && !c->profile) {
     cudaGraphExec_t ex;
@@ -728,6 +735,149 @@ rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
     out->phase_launches[r.slot] += 1;
   }
   return RPCHOL_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+// Layout of a checkpoint (host memory, native byte order): SaveHeader, the
+// device state, d (N doubles), the tile sums, the pivots (rank int64) and F
+// (N rows x rank columns in the stored dtype, packed).
+struct SaveHeader {
+  char magic[8];
+  int32_t version, precision, kind, d;
+  int64_t N, k_max, rank, bytes;
+  double sigma;
+  int64_t ntiles, elem;
+};
+
+static size_t save_bytes(const rpchol_ctx* c, long long rank) {
+  const size_t es = c->b.mixed ? sizeof(float) : sizeof(double);
+  return sizeof(SaveHeader) + sizeof(DevState) + sizeof(double) * (size_t)c->b.N +
+         sizeof(double) * (size_t)c->b.ntiles + sizeof(long long) * (size_t)rank +
+         es * (size_t)c->b.N * (size_t)rank;
+}
+
+rpchol_status rpchol_save(rpchol_ctx* c, void* host_buf, size_t* bytes) {
+  g_err[0] = 0;
+  if (!c || !bytes) return RPCHOL_EINVAL;
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  if (!c->has_run) {
+    set_err("nothing to save: the context has not run");
+    return RPCHOL_EINVAL;
+  }
+  const DevState st = *c->st_host;
+  const long long rank = st.rank;
+  const size_t need = save_bytes(c, rank);
+  if (!host_buf) {
+    *bytes = need;
+    return RPCHOL_OK;
+  }
+  if (*bytes < need) {
+    set_err("buffer of %zu bytes, %zu needed", *bytes, need);
+    *bytes = need;
+    return RPCHOL_EINVAL;
+  }
+  char* p = (char*)host_buf;
+  SaveHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "RPCHOLS1", 8);
+  h.version = 1;
+  h.precision = c->precision;
+  h.kind = c->b.kind;
+  h.d = c->b.d;
+  h.N = c->b.N;
+  h.k_max = c->k_max;
+  h.rank = rank;
+  h.bytes = (int64_t)need;
+  h.sigma = c->b.sigma;
+  h.ntiles = c->b.ntiles;
+  h.elem = c->b.mixed ? 4 : 8;
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  memcpy(p, &st, sizeof(DevState));
+  p += sizeof(DevState);
+  const size_t es = (size_t)h.elem;
+  CU(cudaMemcpyAsync(p, c->b.dvec, sizeof(double) * c->b.N, cudaMemcpyDeviceToHost, c->stream));
+  p += sizeof(double) * c->b.N;
+  CU(cudaMemcpyAsync(p, c->b.tile_sums, sizeof(double) * c->b.ntiles, cudaMemcpyDeviceToHost,
+                     c->stream));
+  p += sizeof(double) * c->b.ntiles;
+  if (rank > 0) {
+    CU(cudaMemcpyAsync(p, c->b.piv, sizeof(long long) * rank, cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(long long) * rank;
+    CU(cudaMemcpy2DAsync(p, es * rank, c->b.F, es * c->b.ldF, es * rank, c->b.N,
+                         cudaMemcpyDeviceToHost, c->stream));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  *bytes = need;
+  return RPCHOL_OK;
+}
+
+rpchol_status rpchol_restore(rpchol_ctx* c, const void* host_buf, size_t bytes) {
+  g_err[0] = 0;
+  if (!c || !host_buf || bytes < sizeof(SaveHeader) + sizeof(DevState)) return RPCHOL_EINVAL;
+  const char* p = (const char*)host_buf;
+  SaveHeader h;
+  memcpy(&h, p, sizeof(h));
+  if (memcmp(h.magic, "RPCHOLS1", 8) != 0 || h.version != 1) {
+    set_err("not a checkpoint of this library");
+    return RPCHOL_EINVAL;
+  }
+  if (h.N != c->b.N || h.d != c->b.d || h.kind != c->b.kind || h.sigma != c->b.sigma ||
+      h.precision != c->precision || h.ntiles != c->b.ntiles || h.rank > c->k_max ||
+      h.rank < 0 || (size_t)h.bytes != bytes || save_bytes(c, h.rank) != bytes) {
+    set_err("checkpoint does not match this context (N, d, kernel, sigma, precision, k_max)");
+    return RPCHOL_EINVAL;
+  }
+  p += sizeof(h);
+  DevState st;
+  memcpy(&st, p, sizeof(DevState));
+  p += sizeof(DevState);
+  if (st.rank != h.rank || st.T < 1 || st.T > c->b.Tmax) {
+    set_err("checkpoint state does not fit this context (T_max)");
+    return RPCHOL_EINVAL;
+  }
+  const size_t es = (size_t)h.elem;
+  const long long rank = h.rank;
+  CU(cudaMemcpyAsync(c->b.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->b.dvec, p, sizeof(double) * c->b.N, cudaMemcpyHostToDevice, c->stream));
+  p += sizeof(double) * c->b.N;
+  CU(cudaMemcpyAsync(c->b.tile_sums, p, sizeof(double) * c->b.ntiles, cudaMemcpyHostToDevice,
+                     c->stream));
+  p += sizeof(double) * c->b.ntiles;
+  if (rank > 0) {
+    CU(cudaMemcpyAsync(c->b.piv, p, sizeof(long long) * rank, cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(long long) * rank;
+    CU(cudaMemcpy2DAsync(c->b.F, es * c->b.ldF, p, es * rank, es * rank, c->b.N,
+                         cudaMemcpyHostToDevice, c->stream));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  *c->st_host = st;
+  c->has_run = 1;
+  c->last_plain = st.plain;
+  clear_prof(c);
+  c->host_iters = -1;
+  return RPCHOL_OK;
+}
+
+rpchol_status rpchol_resume(rpchol_ctx* c, int64_t k) {
+  g_err[0] = 0;
+  if (!c) return RPCHOL_EINVAL;
+  rpchol_status s = read_state(c);
+  if (s != RPCHOL_OK) return s;
+  DevState st = *c->st_host;
+  if (!c->has_run || k <= st.rank || k > c->k_max || st.status != 0) {
+    set_err("invalid resume: k=%lld rank=%lld k_max=%lld status=%d", (long long)k, st.rank,
+            c->k_max, st.status);
+    return RPCHOL_EINVAL;
+  }
+  st.k = k;
+  st.done = 0;
+  st.max_rounds = st.round + (st.plain ? 2 * (k - st.rank) : 4 * (k - st.rank)) + 64;
+  CU(cudaMemcpyAsync(c->b.st, &st, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  clear_prof(c);
+  return run_loop(c, st.plain, st.T, st.max_rounds - st.round);
 }
 
 void rpchol_destroy(rpchol_ctx* c) {

@@ -101,3 +101,12 @@ def test_invalid_arguments_of_the_other_algorithms(library):
     assert L.rpchol_rpqr_run(None, 1, 1, 0) == 1
     assert L.rpchol_rpqr_copy(None, None, 0, None, 0, None, None, None, None) == 1
     assert L.rpchol_rpqr_destroy(None) == 0
+
+
+def test_checkpoint_calls_reject_bad_arguments(library):
+    L = rp.lib()
+    n = ctypes.c_size_t(0)
+    assert L.rpchol_save(None, None, ctypes.byref(n)) == 1
+    buf = ctypes.create_string_buffer(16)
+    assert L.rpchol_restore(None, buf, 16) == 1
+    assert L.rpchol_resume(None, 10) == 1
