@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
                                               const TF* __restrict__ F, long long ldF,
                                               const int* __restrict__ prop, double* H,
                                               double* Hpart, int* hcnt) {
-  __shared__ double Fa[16][33];
-  __shared__ double Fb[16][33];
+  __shared__ TF Fa[16][33];
+  __shared__ TF Fb[16][33];
   __shared__ int last;
   if (st->done) return;
   const int T = st->T;
@@ -293,20 +293,40 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
     const int a = a0 + (e >> 4), bb = b0 + (e & 15);
     if (a < T && bb < T && bb <= a) P[KS * 256 + e] = kval(a, bb);
   }
+  // FP32 factor (mixed mode): the products of FP32 entries are summed as
+  // unevaluated float pairs (exact product by FMA, two-sum of Knuth) on the
+  // FP32 pipe, which on this GPU issues far more than the FP64 one; about 48
+  // bits survive, well below the FP32 rounding of F itself
+  float sh = 0.f, sl = 0.f;
   for (long long m0 = m_lo; m0 < m_hi; m0 += 32) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int r = (tid + 256 * q) >> 5;
-      Fa[r][cc] = (double)va[q];
-      Fb[r][cc] = (double)vb[q];
+      Fa[r][cc] = va[q];
+      Fb[r][cc] = vb[q];
     }
     __syncthreads();
     if (m0 + 32 < m_hi) fetch(m0 + 32);
     const int qn = m_hi - m0 < 32 ? (int)(m_hi - m0) : 32;
+    if constexpr (sizeof(TF) == 4) {
 #pragma unroll 8
-    for (int q = 0; q < qn; ++q) acc = fma(Fa[ty][q], Fb[tx][q], acc);
+      for (int q = 0; q < qn; ++q) {
+        const float a = Fa[ty][q], b = Fb[tx][q];
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        const float t = __fadd_rn(sh, p);
+        const float bp = __fsub_rn(t, sh);
+        const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(er, e));
+      }
+    } else {
+#pragma unroll 8
+      for (int q = 0; q < qn; ++q) acc = fma(Fa[ty][q], Fb[tx][q], acc);
+    }
     __syncthreads();
   }
+  if constexpr (sizeof(TF) == 4) acc = (double)sh + (double)sl;
   double sum = acc;
   if (KS > 1) {
     P[z * 256 + tid] = acc;
