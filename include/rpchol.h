@@ -80,8 +80,10 @@ typedef enum {
 /* FP64: every step in IEEE double (parity mode).
  * MIXED: F stored in FP32; the kernel-column and Schur contractions run in
  * single-precision arithmetic with FP32 accumulation (compensated split
- * products on the tensor-core path); the T x T rejection-sampling Cholesky,
- * L^{-1} and the residual-diagonal accumulation stay in FP64.             */
+ * products on the tensor-core path); H is stored in FP64, its F(S',:) F(S',:)^*
+ * part summed as float pairs (about 48 significant bits); the T x T
+ * rejection-sampling Cholesky, L^{-1} and the residual-diagonal
+ * accumulation stay in FP64.                                               */
 typedef enum { RPCHOL_FP64 = 0, RPCHOL_MIXED = 1 } rpchol_precision;
 
 typedef enum { RPCHOL_DT_F32 = 0, RPCHOL_DT_F64 = 1 } rpchol_dtype;
