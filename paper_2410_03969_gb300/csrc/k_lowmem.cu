@@ -521,6 +521,9 @@ rpchol_status rpchol_lowmem_run(rpchol_lowmem* c, int64_t k, int32_t T, uint64_t
     return RPCHOL_EINVAL;
   }
   const long long max_rounds = 4 * k + 64;
+  // rows of an earlier, longer run may hold entries right of the diagonal:
+  // the copied-out factor starts from zeros
+  LMCU(cudaMemsetAsync(c->Lr, 0, sizeof(double) * (size_t)c->k_max * c->ldL, c->stream));
   LMCU(launch_reset(c->b, k, T, seed, 0u, 0, max_rounds, c->stream));
   c->has_run = 1;
   for (long long it = 0; it < max_rounds + 1;) {
@@ -554,11 +557,6 @@ rpchol_status rpchol_lowmem_copy(rpchol_lowmem* c, double* L_out, int64_t ld_out
     LMCU(cudaMemcpyAsync(d_out, c->b.dvec, sizeof(double) * c->b.N, cudaMemcpyDefault,
                          c->stream));
   LMCU(cudaStreamSynchronize(c->stream));
-  // the factor is lower triangular: rows written in earlier, longer runs
-  // may hold entries right of the diagonal
-  if (L_out)
-    for (long long i = 0; i < rank; ++i)
-      for (long long j = i + 1; j < rank; ++j) L_out[i * ld_out + j] = 0.0;
   if (rank_out) *rank_out = rank;
   if (rounds_out) *rounds_out = c->has_run ? c->st_host->round : 0;
   return c->has_run ? lm_status(*c->st_host) : RPCHOL_OK;
