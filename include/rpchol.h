@@ -249,6 +249,17 @@ rpchol_status rpchol_restore(rpchol_ctx* ctx, const void* host_buf, size_t bytes
  * status must be OK.  Asynchronous like rpchol_run.  Errors: EINVAL.       */
 rpchol_status rpchol_resume(rpchol_ctx* ctx, int64_t k);
 
+/* Failure-detection self-test: two one-thread kernels each wait on an
+ * mbarrier that nothing completes, one with the CTA-scope bounded wait of
+ * the tensor-core column step, one with the cluster-scope bounded wait of
+ * Algorithm 1.  Each wait must give up after limit_ms (1..2000) and report
+ * it; the kernels then return and the CUDA context stays usable.  Returns
+ * RPCHOL_ETIMEOUT when both waits expired as designed (the expected
+ * outcome; waited_ms[0..1], if not NULL, receives the two waiting times),
+ * ECUDA if one did not report its expiry or a CUDA call failed, EINVAL for
+ * limit_ms out of range.  Synchronous, on the legacy default stream.       */
+rpchol_status rpchol_selftest_wait(uint32_t limit_ms, double* waited_ms);
+
 /* Release everything the context owns.  NULL is accepted.  A batch that
  * holds the context must be destroyed first.                              */
 void rpchol_destroy(rpchol_ctx* ctx);

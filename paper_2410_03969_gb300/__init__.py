@@ -82,6 +82,7 @@ _SIGNATURES = [
                                    ctypes.POINTER(ctypes.c_size_t)]),
     ("rpchol_restore", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("rpchol_resume", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("rpchol_selftest_wait", ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]),
     ("rpchol_trace_error_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                                   ctypes.c_int64, ctypes.c_int64,
                                                   ctypes.c_int64, ctypes.c_void_p,

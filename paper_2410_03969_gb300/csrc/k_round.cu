@@ -744,6 +744,31 @@ __global__ void __cluster_dims__(kRejCluster, 1, 1) __launch_bounds__(kRejectThr
   }
 }
 
+// Failure-detection self-test: one thread waits, with the cluster-scope
+// bounded wait of Algorithm 1, on a barrier that nothing completes; the wait
+// must give up after limit_ns.  out[0] = 1 if it gave up, out[1] = the time
+// it waited (ns).
+__global__ void k_wait_selftest_cluster(unsigned long long limit_ns, unsigned long long* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(&bar))
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  unsigned long long t0, t1;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  const bool ok = wait_cluster_bounded(&bar, 0u, limit_ns);
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+  out[0] = ok ? 0ull : 1ull;
+  out[1] = t1 - t0;
+}
+
+cudaError_t launch_wait_selftest_cluster(unsigned long long limit_ns, unsigned long long* out,
+                                         cudaStream_t s) {
+  k_wait_selftest_cluster<<<1, 32, 0, s>>>(limit_ns, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s) {
   // packed rows of the CTA that owns the most
   size_t most = 0;

@@ -880,6 +880,34 @@ rpchol_status rpchol_resume(rpchol_ctx* c, int64_t k) {
   return run_loop(c, st.plain, st.T, st.max_rounds - st.round);
 }
 
+rpchol_status rpchol_selftest_wait(uint32_t limit_ms, double* waited_ms) {
+  g_err[0] = 0;
+  if (limit_ms < 1 || limit_ms > 2000) {
+    set_err("limit_ms must be in [1, 2000]");
+    return RPCHOL_EINVAL;
+  }
+  unsigned long long* dout = nullptr;
+  unsigned long long h[4] = {0, 0, 0, 0};
+  CU(cudaMalloc((void**)&dout, sizeof(h)));
+  const unsigned long long lim = 1000000ull * limit_ms;
+  cudaError_t e = launch_wait_selftest_cta(lim, dout, nullptr);
+  if (e == cudaSuccess) e = launch_wait_selftest_cluster(lim, dout + 2, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h, dout, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+  if (waited_ms) {
+    waited_ms[0] = (double)h[1] * 1e-6;
+    waited_ms[1] = (double)h[3] * 1e-6;
+  }
+  if (h[0] == 1 && h[2] == 1) {
+    set_err("both bounded waits gave up after %.1f and %.1f ms, as designed", h[1] * 1e-6,
+            h[3] * 1e-6);
+    return RPCHOL_ETIMEOUT;
+  }
+  set_err("a bounded wait did not report its expiry");
+  return RPCHOL_ECUDA;
+}
+
 void rpchol_destroy(rpchol_ctx* c) {
   if (!c) return;
   release_all(c);

@@ -110,3 +110,8 @@ def test_checkpoint_calls_reject_bad_arguments(library):
     buf = ctypes.create_string_buffer(16)
     assert L.rpchol_restore(None, buf, 16) == 1
     assert L.rpchol_resume(None, 10) == 1
+
+
+def test_selftest_limit_is_checked_before_any_launch(library):
+    assert rp.lib().rpchol_selftest_wait(0, None) == 1
+    assert rp.lib().rpchol_selftest_wait(2001, None) == 1
