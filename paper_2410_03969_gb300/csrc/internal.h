@@ -110,11 +110,6 @@ cudaError_t add_reset_params_node(cudaGraph_t g, const DevBuffers& b, const RunP
 cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_reject(const DevBuffers& b, int T, cudaStream_t s);
-// bounded-wait self-tests (out: 2 words in device memory)
-cudaError_t launch_wait_selftest_cluster(unsigned long long limit_ns, unsigned long long* out,
-                                         cudaStream_t s);
-cudaError_t launch_wait_selftest_cta(unsigned long long limit_ns, unsigned long long* out,
-                                     cudaStream_t s);
 cudaError_t launch_gather_f64(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_round_end(const DevBuffers& b, unsigned long long cond, int use_cond,
                              cudaStream_t s);

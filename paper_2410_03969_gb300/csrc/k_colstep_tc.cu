@@ -710,30 +710,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-// Failure-detection self-test: one thread waits, with the CTA-scope bounded
-// wait of the column step's pipeline, on a barrier that nothing completes.
-// out[0] = 1 if it gave up (and raised its abort flag), out[1] = the time it
-// waited (ns).
-__global__ void k_wait_selftest_cta(unsigned long long limit_ns, unsigned long long* out) {
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ int abort_flag;
-  if (threadIdx.x != 0) return;
-  abort_flag = 0;
-  tc::mbar_init(&bar, 1);
-  tc::fence_mbarrier_init();
-  const unsigned long long t0 = tc::globaltimer_ns();
-  const bool ok = tc::mbar_wait_bounded(&bar, 0u, limit_ns, &abort_flag);
-  const unsigned long long t1 = tc::globaltimer_ns();
-  out[0] = (!ok && abort_flag) ? 1ull : 0ull;
-  out[1] = t1 - t0;
-}
-
-cudaError_t launch_wait_selftest_cta(unsigned long long limit_ns, unsigned long long* out,
-                                     cudaStream_t s) {
-  k_wait_selftest_cta<<<1, 32, 0, s>>>(limit_ns, out);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, unsigned long long cond,
                               int use_cond, cudaStream_t s) {
   static bool attr_set = false;

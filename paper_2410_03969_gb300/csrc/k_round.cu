@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "selftest.h"
 
 namespace rpchol {
 

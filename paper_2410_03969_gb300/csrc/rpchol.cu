@@ -16,6 +16,7 @@
 
 #include "../../include/rpchol.h"
 #include "internal.h"
+#include "selftest.h"
 
 using namespace rpchol;
 
