@@ -115,3 +115,26 @@ def test_checkpoint_calls_reject_bad_arguments(library):
 def test_selftest_limit_is_checked_before_any_launch(library):
     assert rp.lib().rpchol_selftest_wait(0, None) == 1
     assert rp.lib().rpchol_selftest_wait(2001, None) == 1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/rpchol.h compiles as C11 (no C++ or torch types cross the
+    boundary) and a C program linking every declared entry point links."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    names = declared_symbols()
+    src = tmp_path / "use.c"
+    body = "\n".join("    (void *)&%s," % n for n in names)
+    src.write_text('#include "rpchol.h"\n#include <stddef.h>\n'
+                   "void *table[] = {\n%s\n    NULL};\nint main(void) { return table[0] == NULL; }\n"
+                   % body)
+    rpbuild.build()
+    out = tmp_path / "use"
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(out), rpbuild.LIB,
+                        "-Wl,-rpath," + os.path.dirname(rpbuild.LIB)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
