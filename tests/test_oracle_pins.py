@@ -441,6 +441,50 @@ def test_rpqr_meets_rpcholesky_on_the_gram_matrix(T):
     assert np.max(np.abs(R[:, S])) <= 1e-10 * np.max(np.abs(B))
 
 
+def _rpqr_algorithm4_numpy(B, k, seed):
+    """Algorithm 4 (randomly pivoted QR, one pivot per step) restated with
+    numpy: draw s from u / sum(u) (searchsorted on the cumulative sums, the
+    same Philox uniforms), q = normalised residual column, F(:,i) = B^* q,
+    u -= F(:,i)^2 clamped at 0."""
+    M, N = B.shape
+    u = np.sum(B * B, axis=0)
+    Q = np.zeros((M, k))
+    F = np.zeros((N, k))
+    S = []
+    for i in range(k):
+        up, _ = oracle.uniform_pair(seed, 0, i)
+        C = np.cumsum(u)
+        s = int(np.searchsorted(C, up * C[-1], side="right"))
+        g = B[:, s] - Q[:, :i] @ F[s, :i]
+        q = g / np.linalg.norm(g)
+        Q[:, i] = q
+        F[:, i] = B.T @ q
+        u = np.maximum(u - F[:, i] ** 2, 0.0)
+        S.append(s)
+    return Q, F, S, u
+
+
+def test_rpqr_block_one_is_algorithm_4():
+    rng = np.random.default_rng(26)
+    B = rng.standard_normal((30, 5)) @ rng.standard_normal((5, 50)) + 0.1 * rng.standard_normal((30, 50))
+    k, seed = 20, 3
+    qr = oracle.rpqr_accel(B, k, 1, seed)
+    Q, F, S, u = _rpqr_algorithm4_numpy(B, k, seed)
+    assert list(qr["S"]) == S
+    assert np.max(np.abs(qr["F"] - F)) <= 1e-10 * np.max(np.abs(F))
+    assert np.max(np.abs(qr["Q"] - Q)) <= 1e-10
+    assert np.max(np.abs(qr["u"] - u)) <= 1e-10 * np.max(np.sum(B * B, axis=0))
+
+
+def test_lowmem_block_one_is_simple_rpcholesky():
+    X = np.random.default_rng(27).standard_normal((200, 4)).astype(np.float32)
+    lo = oracle.rpc_lowmem(30, 1, 6, X=X, kernel="laplace_l2", sigma=1.5)
+    pl = oracle.rpc_plain(30, 6, X=X, kernel="laplace_l2", sigma=1.5)
+    assert list(lo["S"]) == list(pl["S"])
+    assert np.max(np.abs(lo["L"] - pl["F"][pl["S"], :])) <= 1e-12
+    assert np.max(np.abs(lo["d"] - pl["d"])) <= 1e-12
+
+
 def test_rpqr_full_rank_exhaustion():
     B = np.random.default_rng(25).standard_normal((5, 9))
     qr = oracle.rpqr_accel(B, 5, 4, 1)
