@@ -229,7 +229,9 @@ rpchol_status rpchol_trace_error_noalloc(const void* F_dev, int32_t F_dtype, int
                                          int64_t ldF, int64_t rank, double* out_dev,
                                          void* stream);
 
-/* Checkpoints.  rpchol_save writes the state of the last run (run state,
+/* Checkpoints (no counterpart in the paper; the state saved is that of
+ * Algorithm 2's loop between rounds).  rpchol_save writes the state of the
+ * last run (run state,
  * residual diagonal, tile sums, pivots and the rank columns of F in the
  * stored dtype) to host_buf; with host_buf NULL it only sets *bytes to the
  * size needed.  Synchronous.  rpchol_restore loads such a buffer into a
@@ -249,7 +251,8 @@ rpchol_status rpchol_restore(rpchol_ctx* ctx, const void* host_buf, size_t bytes
  * status must be OK.  Asynchronous like rpchol_run.  Errors: EINVAL.       */
 rpchol_status rpchol_resume(rpchol_ctx* ctx, int64_t k);
 
-/* Failure-detection self-test: two one-thread kernels each wait on an
+/* Failure-detection self-test (no counterpart in the paper): two
+ * one-thread kernels each wait on an
  * mbarrier that nothing completes, one with the CTA-scope bounded wait of
  * the tensor-core column step, one with the cluster-scope bounded wait of
  * Algorithm 1.  Each wait must give up after limit_ms (1..2000) and report
