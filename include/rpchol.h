@@ -130,6 +130,10 @@ typedef struct {
     int64_t phase_launches[8];
     int64_t kernel_launches; /* kernels the last run launched on the device (the
                                 reset kernel plus every kernel of every loop body) */
+    double mma_flops_tf32;   /* tensor-core flops the column steps executed with
+                                tcgen05.mma kind::tf32 (split terms and padding
+                                included), 0 on the CUDA-core paths */
+    double mma_flops_f16;    /* the same for kind::f16 */
 } rpchol_run_stats;
 
 typedef struct rpchol_ctx rpchol_ctx;
@@ -218,9 +222,11 @@ rpchol_status rpchol_stats(rpchol_ctx* ctx, rpchol_run_stats* out);
  *   stream   cudaStream_t (NULL = legacy default stream); asynchronous
  * Scratch: per-tile partial sums in a static device array of 65,536 doubles
  * (512 KiB) that every GPU loading the library keeps until the process
- * exits; N > 8,388,608 is rejected with RPCHOL_EINVAL.  The first call on a
- * device looks up the array's address on that device (make it before any
- * stream capture on that device).  All calls share the array: calls whose
+ * exits; N > 8,388,608 is rejected with RPCHOL_EINVAL.  Every call looks
+ * up the array's address on the current device (nothing is cached, so a
+ * device reset between calls is harmless); the first call on a device loads
+ * the module there, so make it before any stream capture on that device.
+ * All calls share the array: calls whose
  * kernels overlap on the GPU race, so serialise them.  Each call overwrites
  * every partial it uses, so no state carries over between calls.
  * Errors: EINVAL (null pointer, N < 1, rank < 0, ldF < rank, bad dtype,

@@ -40,7 +40,8 @@ class RunStats(ctypes.Structure):
                 ("residual_trace", ctypes.c_double), ("trace_error", ctypes.c_double),
                 ("col_bytes", ctypes.c_double), ("col_flops", ctypes.c_double),
                 ("phase_ms", ctypes.c_double * 8), ("phase_launches", ctypes.c_int64 * 8),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("mma_flops_tf32", ctypes.c_double),
+                ("mma_flops_f16", ctypes.c_double)]
 
 PHASES = ("propose", "H", "reject", "prep", "colstep", "round_end", "plain_gemv", "plain_finish")
 

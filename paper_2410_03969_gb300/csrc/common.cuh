@@ -24,6 +24,7 @@ enum StatusBits : int {
   kStRoundLimit = 1,   // round limit reached before rank k
   kStNumeric = 2,      // non-finite / non-positive pivot
   kStTimeout = 4,      // a bounded device-side wait expired
+  kStGateExpired = 8,  // profile mode: the stream gate gave up waiting for the host
 };
 
 // Run state, one per context, in device memory.  Written only by
@@ -49,6 +50,8 @@ struct DevState {
   long long piv;         // simple RPCholesky: pivot of the current step
   double col_bytes;      // algorithmic bytes of the column-step kernels so far
   double col_flops;      // algorithmic flops of the column-step kernels so far
+  double mma_tf32;       // tensor-core flops the column steps executed, kind::tf32
+  double mma_f16;        // tensor-core flops the column steps executed, kind::f16
 };
 
 // Parameters of one run, read by the reset kernel of a batched launch (so

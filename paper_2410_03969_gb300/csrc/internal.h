@@ -79,12 +79,17 @@ struct DevBuffers {
 // Algorithm 6): bookkeeping of the round, the stopping test (rank k reached,
 // or the round limit), and the WHILE condition of the graph.  One thread,
 // after every kernel of the round has finished with the state.
+// `mma_tf32` / `mma_f16`: tensor-core flops the round's column step
+// executed (zero for the CUDA-core column steps).
 __device__ __forceinline__ void round_end_body(DevState* st, unsigned long long cond, int use_cond,
-                                               long long N, int d, int bF) {
+                                               long long N, int d, int bF, double mma_tf32 = 0.0,
+                                               double mma_f16 = 0.0) {
   if (!st->done) {
     const double n = (double)N, r = (double)st->rank, sc = (double)st->s;
     st->col_bytes += n * (r * bF + sc * bF + 4.0 * d + 16.0);
     st->col_flops += 2.0 * n * r * sc + n * sc * sc + 3.0 * n * d * sc;
+    st->mma_tf32 += mma_tf32;
+    st->mma_f16 += mma_f16;
     st->rank += st->s;
     st->round += 1;
     st->proposals += st->T;

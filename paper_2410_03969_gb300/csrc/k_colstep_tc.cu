@@ -704,7 +704,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __threadfence();
     if (atomicAdd(a.ccnt, 1u) == gridDim.x - 1) {
       __threadfence();
-      round_end_body(st, a.cond, a.use_cond, a.N, a.d, 4);
+      // three split products per K step, M = 128 rows per tile, N = s_pad
+      const double mma = 6.0 * 128.0 * (double)ntiles * (double)s_pad * (double)(nch * kKc);
+      round_end_body(st, a.cond, a.use_cond, a.N, a.d, 4, mma, 0.0);
       *a.ccnt = 0u;
     }
   }

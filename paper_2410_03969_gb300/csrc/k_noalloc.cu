@@ -11,9 +11,12 @@
 // loads the library holds it until the process exits).
 //
 // Behaviour a caller must know:
-//   - The first call on a device looks up that device's address of the
-//     array (cudaGetSymbolAddress, with that device current) and caches it;
-//     make that first call before any stream capture on the device.
+//   - Every call looks up the current device's address of the array
+//     (cudaGetSymbolAddress, with that device current).  The lookup
+//     enqueues no work and is not cached, so a context that was torn down
+//     and created again (cudaDeviceReset) is looked up afresh.  The first
+//     call on a device loads the module there; make it before any stream
+//     capture on that device.
 //   - Every call shares the one array; calls whose kernels overlap on the
 //     GPU race on it.  Serialise them (one stream, or events).
 //   - Each call overwrites every partial it reads, so nothing needs to start
@@ -22,7 +25,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/rpchol.h"
 #include "internal.h"
@@ -35,10 +37,6 @@ constexpr long long kNoAllocMaxTiles = 65536;
 constexpr long long kNoAllocMaxRows = kNoAllocTileRows * kNoAllocMaxTiles;  // 8,388,608
 
 static __device__ __align__(256) double g_trace_partials[kNoAllocMaxTiles];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_partials_addr[kMaxDevices] = {};
 
 // One CTA per 128-row tile: part[tile] = sum over its rows of
 // (1 - ||F(r, 0:rank)||^2) (phi(0) = 1 on the diagonal of A), fixed order.
@@ -105,28 +103,16 @@ extern "C" rpchol_status rpchol_trace_error_noalloc(const void* F_dev, int32_t F
              (long long)N, kNoAllocMaxRows);
     return RPCHOL_EINVAL;
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    set_last_error( "rpchol_trace_error_noalloc: device query: %s",
-             cudaGetErrorString(e));
+  // the current device's address of the array: looked up on every call (no
+  // cache to go stale across a context reset; the lookup enqueues nothing)
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_trace_partials);
+  if (e != cudaSuccess || !p) {
+    set_last_error("rpchol_trace_error_noalloc: cudaGetSymbolAddress: %s",
+                   cudaGetErrorString(e));
     return RPCHOL_ECUDA;
   }
-  double* part = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_partials_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_trace_partials);  // device `dev` is current
-      if (e != cudaSuccess || !p) {
-        set_last_error(
-                 "rpchol_trace_error_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        return RPCHOL_ECUDA;
-      }
-      g_partials_addr[dev] = (double*)p;
-    }
-    part = g_partials_addr[dev];
-  }
+  double* part = (double*)p;
   const long long ntiles = (N + kNoAllocTileRows - 1) / kNoAllocTileRows;
   cudaStream_t s = (cudaStream_t)stream;
   if (F_dtype == RPCHOL_DT_F32)

@@ -43,6 +43,8 @@ __device__ __forceinline__ void reset_run(DevState* st, double* dvec, double* ti
     st->piv = -1;
     st->col_bytes = 0.0;
     st->col_flops = 0.0;
+    st->mma_tf32 = 0.0;
+    st->mma_f16 = 0.0;
   }
 }
 

@@ -286,14 +286,17 @@ rpchol_status get_graph(rpchol_ctx* c, int plain, int T, cudaGraphExec_t* out) {
 // Profile mode holds the stream at a gate until a whole chunk of rounds (the
 // kernels and the events around them) is enqueued, so that the events time
 // the kernels back to back rather than the host's enqueue rate.  The gate
-// polls a pinned host flag for at most about a second.
-__global__ void k_gate(const int* flag, int target) {
+// polls a pinned host flag for at most about a second; if it gives up, it
+// sets kStGateExpired in the run status (the phase times of that run then
+// include host enqueue time, and the run reports RPCHOL_ETIMEOUT).
+__global__ void k_gate(const int* flag, int target, int* status) {
   for (int i = 0; i < 1000000; ++i) {
     int v;
     asm volatile("ld.relaxed.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
     if (v >= target) return;
     __nanosleep(1000);
   }
+  atomicOr(status, (int)kStGateExpired);
 }
 
 void clear_prof(rpchol_ctx* c) {
@@ -338,7 +341,8 @@ rpchol_status run_loop(rpchol_ctx* c, int plain, int T, long long max_rounds) {
   for (long long it = 0; it < max_rounds + 1;) {
     const long long chunk = plain ? 64 : 8;
     if (c->profile) {
-      k_gate<<<1, 1, 0, c->stream>>>(c->gate_dev, ++c->gate_gen);
+      k_gate<<<1, 1, 0, c->stream>>>(c->gate_dev, ++c->gate_gen,
+                                     (int*)((char*)c->b.st + offsetof(DevState, status)));
       CU(cudaGetLastError());
     }
     for (long long j = 0; j < chunk; ++j, ++it) {
@@ -372,6 +376,11 @@ rpchol_status status_of(const DevState& s) {
   if (s.status & kStNumeric) {
     set_err("non-positive pivot or non-finite value met on the device");
     return RPCHOL_ENUMERIC;
+  }
+  if (s.status & kStGateExpired) {
+    set_err("profile mode: the stream gate gave up waiting for the host, so the phase "
+            "times include host enqueue time");
+    return RPCHOL_ETIMEOUT;
   }
   if (s.status & kStRoundLimit) {
     set_err("round limit reached before the target rank");
@@ -715,6 +724,8 @@ rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
   out->trace_error = host[0] / (double)c->b.N;  // tr A = N (phi(0) = 1)
   out->col_bytes = st.col_bytes;
   out->col_flops = st.col_flops;
+  out->mma_flops_tf32 = st.mma_tf32;
+  out->mma_flops_f16 = st.mma_f16;
   {
     // kernels of one loop body: accelerated = propose, H, Algorithm 1, operand
     // prep (prep and W blocks in one launch for the tensor-core step, the

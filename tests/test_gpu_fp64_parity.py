@@ -6,11 +6,14 @@ within 1e-12 (the proposal map's running sum within 1e-12 W of U W, or the
 acceptance ratio h/u within 1e-12 of its uniform).  F must agree to 1e-10
 relative Frobenius error and d to 1e-12 (absolute, A_jj = 1).
 """
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import workloads
+from divergence import accel_divergence, plain_divergence
 
 pytestmark = pytest.mark.gpu
 
@@ -28,26 +31,6 @@ def rp():
     return rp
 
 
-def decision_margin_ok(X, kernel, sigma, k, T, seed, S_gpu, S_orc):
-    """True if the first divergence of the pivot sequences happens at a
-    near-tie of the oracle's proposal map (1e-12 W)."""
-    p = next(i for i in range(min(len(S_gpu), len(S_orc))) if S_gpu[i] != S_orc[i])
-    # replay the oracle up to the round of the divergence and inspect its
-    # proposals' running sums at the GPU's and the oracle's choices
-    out = oracle.rpc_accel(p, T, seed, X=X, kernel=kernel, sigma=sigma) if p > 0 else None
-    d = out["d"] if out is not None else np.ones(X.shape[0])
-    W = float(np.sum(d))
-    C = np.cumsum(d)
-    rnd = out["rounds"] if out is not None else 0
-    for j in range(T):
-        up, _ = oracle.uniform_pair(seed, j, rnd)
-        t = up * W
-        near = np.min(np.abs(C - t)) <= 1e-12 * W
-        if near:
-            return True
-    return False
-
-
 def compare(rp_mod, prob, seed, T, plain=False, precision="fp64"):
     X, kern, sg = prob.X, prob.kernel, prob.sigma
     k = prob.k
@@ -61,16 +44,28 @@ def compare(rp_mod, prob, seed, T, plain=False, precision="fp64"):
 
 
 def assert_parity(g, o, prob, seed, T, plain=False):
-    if g["rank"] != o["rank"] or not np.array_equal(g["S"], o["S"]):
-        assert not plain or True
-        assert decision_margin_ok(prob.X, prob.kernel, prob.sigma, prob.k, T, seed,
-                                  g["S"], o["S"]), "pivot divergence outside the 1e-12 margin"
-        return False
-    Fo, Fg = o["F"], g["F"]
-    err = np.linalg.norm(Fg - Fo) / max(np.linalg.norm(Fo), 1e-300)
-    assert err <= F_TOL, err
-    assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
-    return True
+    """'identical' when the pivot sequences agree (then F to 1e-10 and d to
+    1e-12); otherwise the divergence must be an allowed near-tie, named by
+    the analyser, and the columns of F formed before the round of the
+    divergence must still agree to 1e-10.  Returns the description."""
+    if plain:
+        div = plain_divergence(prob.X, prob.kernel, prob.sigma, prob.k, seed, g["S"], o["S"])
+    else:
+        div = accel_divergence(prob.X, prob.kernel, prob.sigma, prob.k, T, seed, g["S"], o["S"])
+    if div is None:
+        assert g["rank"] == o["rank"]
+        Fo, Fg = o["F"], g["F"]
+        err = np.linalg.norm(Fg - Fo) / max(np.linalg.norm(Fo), 1e-300)
+        assert err <= F_TOL, err
+        assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
+        return "identical"
+    assert div["allowed"], "pivot divergence without a near-tie: %r" % (div,)
+    r0 = div["rank0"]
+    if r0 > 0:
+        Fo, Fg = o["F"][:, :r0], g["F"][:, :r0]
+        err = np.linalg.norm(Fg - Fo) / max(np.linalg.norm(Fo), 1e-300)
+        assert err <= F_TOL, err
+    return "allowed near-tie: %r" % (div,)
 
 
 def small_problem(N, d, kernel, sigma, k, seed=0):
@@ -78,22 +73,43 @@ def small_problem(N, d, kernel, sigma, k, seed=0):
     return workloads.Problem("gauss%d_n%d" % (d, N), X, kernel, sigma, k=k, T=0)
 
 
-@pytest.mark.parametrize("seed", range(6))
-def test_gauss8_n2000_accelerated_matches_oracle(rp, seed):
-    prob = workloads.gauss8_n2000(seed)
-    g, o, st = compare(rp, prob, seed, prob.T)
-    assert assert_parity(g, o, prob, seed, prob.T)
-    assert st["rank"] == prob.k and st["status"] == 0
+def test_gauss8_n2000_accelerated_100_seeds(rp):
+    """The small configuration (N = 2000, d = 8, Gaussian, k = 100, T = 20) on
+    100 seeds: the same points, a fresh Philox stream per seed."""
+    prob = workloads.gauss8_n2000(0)
+    res = []
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
+                       precision="fp64") as f:
+        for seed in range(100):
+            f.run(prob.k, prob.T, seed).sync()
+            g = f.copy_factor()
+            st = f.stats()
+            assert st["rank"] == prob.k and st["status"] == 0
+            o = oracle.rpc_accel(prob.k, prob.T, seed, X=prob.X, kernel=prob.kernel,
+                                 sigma=prob.sigma)
+            res.append(assert_parity(g, o, prob, seed, prob.T))
+    assert sum(r == "identical" for r in res) >= 99, res
+
+
+def test_gauss8_n2000_plain_100_seeds(rp):
+    prob = workloads.gauss8_n2000(0)
+    res = []
+    with rp.Factorizer(prob.X, prob.kernel, prob.sigma, k_max=prob.k, T_max=1,
+                       precision="fp64") as f:
+        for seed in range(100):
+            f.run_plain(prob.k, seed).sync()
+            g = f.copy_factor()
+            o = oracle.rpc_plain(prob.k, seed, X=prob.X, kernel=prob.kernel, sigma=prob.sigma)
+            res.append(assert_parity(g, o, prob, seed, 1, plain=True))
+    assert sum(r == "identical" for r in res) >= 99, res
 
 
 @pytest.mark.parametrize("seed", range(3))
-def test_gauss8_n2000_plain_matches_oracle(rp, seed):
-    prob = workloads.gauss8_n2000(seed)
-    g, o, st = compare(rp, prob, seed, 1, plain=True)
-    assert np.array_equal(g["S"], o["S"])
-    err = np.linalg.norm(g["F"] - o["F"]) / np.linalg.norm(o["F"])
-    assert err <= F_TOL
-    assert np.max(np.abs(g["d"] - o["d"])) <= D_TOL
+def test_gauss8_other_point_sets(rp, seed):
+    prob = workloads.gauss8_n2000(seed + 1)
+    g, o, st = compare(rp, prob, seed, prob.T)
+    assert assert_parity(g, o, prob, seed, prob.T) == "identical"
+    assert st["rank"] == prob.k and st["status"] == 0
 
 
 @pytest.mark.parametrize("N,d,kernel,sigma,k,T", [
@@ -108,10 +124,12 @@ def test_gauss8_n2000_plain_matches_oracle(rp, seed):
 ])
 def test_shapes_and_kernels(rp, N, d, kernel, sigma, k, T):
     prob = small_problem(N, d, kernel, sigma, k)
+    res = []
     for seed in (1, 2):
         g, o, st = compare(rp, prob, seed, T)
-        assert_parity(g, o, prob, seed, T)
+        res.append(assert_parity(g, o, prob, seed, T))
         assert st["status"] == 0
+    assert res.count("identical") >= 1, res
 
 
 def test_rank_stops_at_exhaustion(rp):
@@ -155,6 +173,30 @@ def test_repeat_runs_are_deterministic(rp):
         c = f.run(prob.k, prob.T, 6).sync().copy_factor()
     assert np.array_equal(a["S"], b["S"]) and np.array_equal(a["F"], b["F"])
     assert not np.array_equal(a["S"], c["S"])
+
+
+def test_mixture20_n1e5_full_size_matches_oracle(rp):
+    """The N = 1e5 configuration at full size (d = 20 mixture, Gaussian with
+    the median bandwidth, k = 1000, T = 120) in FP64 mode against the oracle
+    (Algorithm 2 with Algorithm 1, all N rows): identical pivots, F to 1e-10
+    relative Frobenius error and d to 1e-12, or an allowed near-tie."""
+    import torch
+    import oracle as orc
+    orc.set_threads(os.cpu_count() or 1)
+    prob = workloads.mixture20_n1e5(0)
+    Xd = torch.from_numpy(prob.X).cuda()
+    res = []
+    for seed in (0, 1):
+        with rp.Factorizer(Xd, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
+                           precision="fp64") as f:
+            f.run(prob.k, prob.T, seed).sync()
+            g = f.copy_factor()
+            st = f.stats()
+        assert st["rank"] == prob.k and st["status"] == 0
+        o = orc.rpc_accel(prob.k, prob.T, seed, X=prob.X, kernel=prob.kernel, sigma=prob.sigma)
+        res.append(assert_parity(g, o, prob, seed, prob.T))
+        del g, o
+    assert res.count("identical") >= 1, res
 
 
 def test_mixture20_full_size_sampled_rows(rp):

@@ -55,6 +55,36 @@ def test_noalloc_trace_error_matches_stats_on_consecutive_calls(env, N, d, k, T)
         assert values[0] != values[1]
 
 
+@pytest.mark.parametrize("N,d,k,T", [(6000, 6, 200, 40)])
+def test_noalloc_fp32_factor_matches_numpy(env, N, d, k, T):
+    """The FP32 factor of mixed mode (the float instantiation of the kernel),
+    on two calls in a row: the value equals 1 - sum of squares of each row of
+    the copied factor, summed in FP64 by numpy (diag A = 1), and rpchol_stats."""
+    torch, rp, fn = env
+    X = workloads.gaussian_cloud(N, d, 4)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    with rp.Factorizer(X, "gaussian", 1.0, k_max=k, T_max=T, precision="mixed") as f:
+        values = []
+        for seed in (3, 4):
+            f.run(k, T, seed).sync()
+            Fp, ld, dt, rank, _ = f.factor_view()
+            assert rank == k and dt == 0  # RPCHOL_DT_F32
+            rc = fn(Fp, dt, N, ld, rank, out.data_ptr(), stream)
+            assert rc == 0, rp.lib().rpchol_last_error()
+            torch.cuda.synchronize()
+            got = float(out.item())
+            Fh = np.empty((N, rank), dtype=np.float32)
+            f.copy_factor_raw(Fh.ctypes.data, rank)
+            rows = 1.0 - np.einsum("ij,ij->i", Fh.astype(np.float64), Fh.astype(np.float64))
+            want = float(np.sum(rows)) / N
+            # both sides sum the same FP32 entries in FP64, in different orders
+            assert got == pytest.approx(want, rel=1e-10, abs=1e-14)
+            assert got == pytest.approx(f.stats()["trace_error"], rel=1e-10, abs=1e-14)
+            values.append(got)
+        assert values[0] != values[1]
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_scratch(env):
     torch, rp, fn = env
     buf = torch.zeros(16, dtype=torch.float64, device="cuda")
