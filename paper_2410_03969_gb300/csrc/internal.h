@@ -12,19 +12,14 @@ namespace rpchol {
 
 // Tensor maps and buffers of the tensor-core column step (mixed mode).
 struct TcMaps {
-  CUtensorMap F;        // F, box 32 x 128
-  CUtensorMap X, Xlo;   // TF32 head / tail planes of X, box 32 x 128
-  CUtensorMap FSh, FSl; // head / tail of F(S,:), box 32 x 64
-  CUtensorMap XSh, XSl; // head / tail of X_S, box 32 x 64
+  CUtensorMap F;        // F, box 32 x 128, 128-byte swizzle
+  CUtensorMap Xh, Xl;   // TF32 head / tail planes of X, box 16 x 128, 64-byte swizzle
   float* Xhp;
   float* Xlp;
-  float* FShp;
-  float* FSlp;
-  float* XShp;
-  float* XSlp;
+  unsigned char* Bf;    // (ldF / 32) chunk images of F(S,:), 128 x kTMax bytes each
+  unsigned char* Bx;    // (xld / 16) chunk images of X_S, 128 x kTMax bytes each
   float* nrmS;          // 256
-  float* Linv32;        // 256 x 256: the round's L in FP32 (lower triangle)
-  float* invd;          // 256: 1 / L(j,j)
+  float* Linv32;        // W blocks of the round (blocked substitution operand)
   int* err;             // status word of the run state
   int num_sms;          // persistent grid size of the column step
 };

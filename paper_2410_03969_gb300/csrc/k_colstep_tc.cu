@@ -2,45 +2,57 @@
 // (Algorithm 2, step 3, arXiv 2410.03969), sm_103a:
 //
 //   D1 = X_tile X_S^*            (fast Euclidean distances, App. A.1)
-//   D2 = F_tile F(S,:)^*         (Schur complement contraction)
-//   R  = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2
+//   R  = kappa(||x||^2 + ||x_S||^2 - 2 D1) - F_tile F(S,:)^*
 //   G L^* = R                    (forward substitution in FP32 with the FP64 L
 //                                 of Algorithm 1 rounded once)
 //   F(tile, rank:rank+s) = G;  d <- max(d - rowsumsq(G), 0) (FP64);  tile sums of d.
 //
-// Both contractions run on tcgen05.mma kind::tf32 with FP32 accumulation in
-// TMEM, as three-term compensated products a_hi b_hi + a_hi b_lo + a_lo b_hi
-// where hi is the TF32 head of an fp32 value (rounded to nearest) and
-// lo = value - hi (exact); this recovers ~fp32 accuracy and with it the
-// cancellation in ||x||^2 + ||y||^2 - 2 x.y and in A - F F^*.  The tensor
-// core's FP32 accumulation truncates, so the F chunks stream from the last
-// column to the first: the small late columns are added first, the large
-// early ones last.
+// One accumulator per 128-row tile holds, in turn, D1, then kappa(D1), then
+// R: the distance contraction runs first; the epilogue maps it to kappa in
+// TMEM; the Schur contraction then accumulates -F_tile F(S,:)^* onto it,
+// the columns of F in forward order, so that the accumulator follows the
+// Schur complement of the growing partial factorisation, whose entries
+// shrink as columns are added (the tensor core's FP32 accumulation
+// truncates; adding to a small accumulator keeps that error small).  With
+// one accumulator of s_pad <= 256 columns per tile, TMEM (512 columns)
+// holds two to four tiles, so the MMAs of later tiles run while the
+// epilogue works on earlier ones, for every block size T <= 256.
 //
-// Persistent kernel: one CTA per SM loops over 128-row tiles (one sampler
+// Precision of the contractions (FP32 accumulation throughout):
+//   - distances: kind::tf32, three-term compensated products
+//     a_hi b_hi + a_hi b_lo + a_lo b_hi of the TF32 head/tail planes of X,
+//     for ~fp32 accuracy in ||x||^2 + ||y||^2 - 2 x.y at any scale of X;
+//   - Schur part: kind::f16 (twice the TF32 rate, half the operand bytes),
+//     the same three-term products of FP16 heads and tails of 4096 F: every
+//     entry of F lies in [-1, 1] (its squared row norm is at most
+//     kappa(x, x) = 1), so 4096 F is far inside the FP16 range and the
+//     head + tail carry 22 significant bits like the TF32 pair; products
+//     carry 4096^2, removed exactly in the epilogue.
+//
+// Persistent kernel: one CTA per SM walks its 128-row tiles (one sampler
 // tile each).  Warp roles (384 threads):
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
-//   warps 2-3   split each fp32 F tile into TF32 head (in place) and tail
-//   warps 4-11  epilogue.  With two tiles in TMEM (s_pad <= 128) warps 4-7
-//               and 8-11 form two groups taking alternate tiles, warp 4 + q
-//               (8 + q) reading TMEM lane quarter q, 4 rows per thread; with
-//               one tile in TMEM all eight work on it, two warps per lane
-//               quarter (16 lanes each), 2 rows per thread.
-// Operands stream through a ring of 2 to 4 shared-memory stages (as many as
-// fit): per stage a 128 x 32 A tile (head, tail) and an s_pad x 32 B tile
-// (head, tail), 128-byte swizzled, K-major.  For s_pad <= 128 the two
-// accumulators of a tile take 256 TMEM columns, so TMEM holds two tiles:
-// the MMAs of the next tile run while an epilogue group works on the last
-// one straight from TMEM (no staging tile in shared memory).  The epilogue
-// evaluates R = kappa - D2 block by block (16 columns), forms G_b with the
-// W blocks, stores G_b back into TMEM over the consumed D1 block (later
-// blocks read it from there) and writes it to F.  For s_pad > 128 one tile
-// holds all of TMEM: tiles alternate with their epilogues, which then
-// use all eight epilogue warps.  Every wait is
-// bounded: on expiry the CTA raises the timeout bit of the run status,
-// drains its own copies and frees its TMEM.
+//   warps 2-3   convert each FP32 F chunk in shared memory, in place, into
+//               FP16 head and tail (interleaved 8-row swizzle atoms)
+//   warps 4-11  epilogue: two groups of four warps taking alternate tiles,
+//               warp 4 + q (8 + q) reading TMEM lane quarter q, 4 rows per
+//               thread.
+// Operands stream through a ring of shared-memory stages, each a 16 KiB A
+// region (128 rows x 128 bytes) and a B region of 2 x s_pad rows x 64
+// bytes.  A stage holds one chunk: 16 coordinates of X (TF32 head and tail
+// planes, by TMA, 64-byte swizzle) against the same 16 of X_S, or 32
+// columns of F (FP32 by TMA, converted in place into 64-byte-swizzled FP16
+// head and tail) against the same 32 of F(S,:).  The B operands of the
+// round are laid out by the operand-prep kernel as the exact shared-memory
+// image of each chunk and arrive with one bulk copy per chunk.  When TMEM
+// holds three or more tiles the producer streams a tile's X chunks one tile
+// ahead of its F chunks, so that the kappa pass of the next tile runs while
+// the current tile's Schur MMAs execute.  Every wait is bounded: on expiry
+// the CTA raises the timeout bit of the run status, drains its own copies
+// and frees its TMEM.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -51,18 +63,21 @@ namespace rpchol {
 namespace {
 constexpr int kTcThreads = 384;
 constexpr int kBM = 128;
-constexpr int kKc = 32;                  // K extent of a chunk (fp32 elements)
-constexpr int kRowBytes = kKc * 4;       // one 128-byte swizzle row per operand row
-constexpr int kStageA = kBM * kRowBytes;  // 16 KiB
-constexpr int kBoxB = 64 * kRowBytes;     // one 64-row box of a B operand, 8 KiB
+constexpr int kStageA = 16384;            // A region of a stage
+constexpr int kFK = 32;                   // columns of F per chunk
+constexpr int kXK = 16;                   // coordinates of X per chunk
 constexpr int kSmemMax = 227 * 1024;
-constexpr int kSmallBytes = 4 * 1024;  // pivots, their norms, barriers, flags, sums
-constexpr int kMaxStages = 4;
-constexpr int kPrefetch = 8;          // A chunks prefetched into L2 ahead of their loads
+constexpr int kSmallBytes = 4 * 1024;     // pivots, their norms, barriers, flags, sums
+constexpr int kMaxStages = 6;
+constexpr int kMaxBuf = 4;                // tiles held in TMEM at once
+constexpr int kPrefetch = 8;              // chunks prefetched into L2 ahead of their loads
+constexpr float kFScale = 4096.f;         // the Schur operands are heads/tails of 4096 F
+constexpr float kAccScale = 16777216.f;   // 4096^2: the scale of the Schur products
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct Layout {
-  int s_pad, nbox, stage_bytes, stages, nbuf, w_resident, w_off, small_off, total;
+  int s_pad, s_alloc, nbuf, look, bbytes, stage_bytes, stages, w_resident, w_off, small_off,
+      total;
 };
 
 // Stages first, then (if room is left for at least as many stages as
@@ -70,9 +85,12 @@ struct Layout {
 __host__ __device__ inline Layout make_layout(int s) {
   Layout L;
   L.s_pad = (s + 15) & ~15;
-  L.nbox = (L.s_pad + 63) >> 6;
-  L.stage_bytes = 2 * kStageA + 2 * L.nbox * kBoxB;
-  L.nbuf = L.s_pad <= 128 ? 2 : 1;
+  L.s_alloc = (L.s_pad + 31) & ~31;
+  L.nbuf = 512 / L.s_alloc;
+  if (L.nbuf > kMaxBuf) L.nbuf = kMaxBuf;
+  L.look = L.nbuf >= 3 ? 1 : 0;
+  L.bbytes = 128 * L.s_pad;
+  L.stage_bytes = kStageA + L.bbytes;
   const int nblk = L.s_pad >> 4;
   const int wbytes = 512 * nblk * (nblk + 1);
   const int budget = kSmemMax - kSmallBytes - 1024;
@@ -89,27 +107,66 @@ __host__ __device__ inline Layout make_layout(int s) {
   return L;
 }
 
-// ---- quad layout: thread t of a warp holds NR rows x 4 columns of each
-// 16-column block (NR = 4: two 16-lane halves of the warp's TMEM quarter,
-// tmem_ld_quad16; NR = 2: one half, tmem_ld_half16), so that the W rows it
-// needs differ between the 4 threads of a quad instead of being one
-// broadcast value.
+// The chunk sequence a CTA streams: for t = 0, 1, ...: the X chunks of
+// local tile t (if t < ntl), then the F chunks of local tile t - look (if
+// t >= look).  A tile whose round has no F columns yet (rank 0) gets one
+// empty F item (kind 2), which loads nothing.  Producer, converter and MMA
+// issuer walk the same sequence.
+struct Seq {
+  int t, ph, c;
+  int ntl, look, nXc, nF;
+  __device__ void init(int ntl_, int look_, int nXc_, int nF_) {
+    ntl = ntl_;
+    look = look_;
+    nXc = nXc_;
+    nF = nF_;
+    t = 0;
+    ph = 0;
+    c = 0;
+    settle();
+  }
+  __device__ bool done() const { return t >= ntl + look; }
+  __device__ int kind() const { return ph == 0 ? 0 : (nF > 0 ? 1 : 2); }
+  __device__ int tile() const { return ph == 0 ? t : t - look; }
+  __device__ void settle() {
+    for (;;) {
+      if (t >= ntl + look) return;
+      if (ph == 0) {
+        if (t < ntl && c < nXc) return;
+        ph = 1;
+        c = 0;
+      }
+      if (t - look >= 0 && c < (nF > 0 ? nF : 1)) return;
+      ph = 0;
+      c = 0;
+      ++t;
+    }
+  }
+  __device__ void next() {
+    ++c;
+    settle();
+  }
+};
+
+// ---- quad layout: thread t of a warp holds 4 rows x 4 columns of each
+// 16-column block (two 16-lane halves of the warp's TMEM quarter,
+// tmem_ld_quad16), so that the W rows it needs differ between the 4
+// threads of a quad instead of being one broadcast value.
 struct EpiQuad {
-  uint32_t d1, d2;       // TMEM D1 / D2 of the warp's lane quarter (column 0)
+  uint32_t acc;          // TMEM accumulator of the warp's lane quarter (column 0)
   const float* W;        // W blocks of the round
   const float* nrmSs;    // squared norms of the round's pivots
   const double* L;       // FP64 Cholesky factor of the round
   float* frow[4];        // F(row ri, rank), nullptr beyond N
   float nr[4];           // squared norms of the rows
   int jpiv[4];           // index among the round's pivots, or -1
-  int s, nF, kind, ldL, cq, lane, even;
+  int s, kind, ldL, cq, lane, even;
   float inv_sigma;
 };
 
 // acc[ri] (columns 2cq..2cq+1 and 8+2cq..9+2cq) += sum over the 16 columns
 // kappa of block X (held across the quad) of X[ri][kappa] W(kappa, col)
-template <int NR>
-__device__ __forceinline__ void quad_fma_block(float2 (&acc)[NR][2], const float (&X)[NR][4],
+__device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float (&X)[4][4],
                                                const float* Wblk, int lane, int cq) {
   const int qbase = lane & ~3;
 #pragma unroll
@@ -119,7 +176,7 @@ __device__ __forceinline__ void quad_fma_block(float2 (&acc)[NR][2], const float
     const float2 w01 = *(const float2*)(Wblk + 16 * kp + 2 * cq);
     const float2 w89 = *(const float2*)(Wblk + 16 * kp + 8 + 2 * cq);
 #pragma unroll
-    for (int ri = 0; ri < NR; ++ri) {
+    for (int ri = 0; ri < 4; ++ri) {
       const float xv = __shfl_sync(0xffffffffu, X[ri][cj], src);
       const float2 x2 = make_float2(xv, xv);
       acc[ri][0] = __ffma2_rn(x2, w01, acc[ri][0]);
@@ -146,79 +203,58 @@ __device__ __forceinline__ float phi_fast(float inv_sigma, float r2) {
   return (1.f + t + t * t * (1.f / 3.f)) * __expf(-t);
 }
 
-template <int KIND, int NR>
-__device__ __forceinline__ void r_quad(const EpiQuad& e, int j0, const float (&D1v)[NR][4],
-                                       const float (&D2v)[NR][4], float (&R)[NR][4]) {
+// The kappa pass: D1 -> 4096^2 kappa(||x||^2 + ||x_S||^2 - 2 D1) in place,
+// columns beyond s zero, kappa(x, x) = 1 at a row's own pivot column.
+template <int KIND>
+__device__ __forceinline__ void kappa_pass(const EpiQuad& e, int nblk) {
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int j0 = 16 * bi;
+    float D1v[4][4], K[4][4];
+    tc::tmem_ld_quad16(e.acc + j0, D1v);
 #pragma unroll
-  for (int cj = 0; cj < 4; ++cj) {
-    const int col = j0 + 8 * (cj >> 1) + 2 * e.cq + (cj & 1);
-    const float ns = e.nrmSs[col];
+    for (int cj = 0; cj < 4; ++cj) {
+      const int col = j0 + 8 * (cj >> 1) + 2 * e.cq + (cj & 1);
+      const float ns = e.nrmSs[col];
 #pragma unroll
-    for (int ri = 0; ri < NR; ++ri) {
-      const float kv =
-          col == e.jpiv[ri] ? 1.f : phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
-      R[ri][cj] = col < e.s ? kv - D2v[ri][cj] : 0.f;
+      for (int ri = 0; ri < 4; ++ri) {
+        const float kv =
+            col == e.jpiv[ri] ? 1.f : phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
+        K[ri][cj] = col < e.s ? kv * kAccScale : 0.f;
+      }
     }
+    tc::tmem_st_quad16(e.acc + j0, K);
   }
 }
 
-// G L^* = R by blocks of 16 columns in the quad layout; finished blocks of G
-// go back into TMEM over the consumed D1 blocks.  Returns each row's
-// Kahan-compensated partial sum of squares (this thread's 4 columns of
-// every block) in rsq / rc.
-template <int NR>
-__device__ __forceinline__ void tmem_ld_rows(uint32_t ta, float (&v)[NR][4]) {
-  if constexpr (NR == 4) tc::tmem_ld_quad16(ta, v);
-  else tc::tmem_ld_half16(ta, v);
-}
-
-template <int NR>
-__device__ __forceinline__ void tmem_st_rows(uint32_t ta, const float (&v)[NR][4]) {
-  if constexpr (NR == 4) tc::tmem_st_quad16(ta, v);
-  else tc::tmem_st_half16(ta, v);
-}
-
-template <int NR>
-__device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (&rsq)[NR],
-                                              float (&rc)[NR]) {
+// G L^* = R by blocks of 16 columns in the quad layout; R is the
+// accumulator divided by 4096^2; finished blocks of G go back into TMEM
+// over the consumed R blocks (later blocks read them from there).  Returns
+// each row's Kahan-compensated partial sum of squares (this thread's 4
+// columns of every block) in rsq / rc.
+__device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (&rsq)[4],
+                                              float (&rc)[4]) {
   const int cq = e.cq;
   for (int bi = 0; bi < nblk; ++bi) {
     const int j0 = 16 * bi;
     const float* Wb = e.W + 128 * bi * (bi + 1);
-    float2 acc[NR][2];
+    float2 acc[4][2];
 #pragma unroll
-    for (int ri = 0; ri < NR; ++ri) acc[ri][0] = acc[ri][1] = make_float2(0.f, 0.f);
+    for (int ri = 0; ri < 4; ++ri) acc[ri][0] = acc[ri][1] = make_float2(0.f, 0.f);
     for (int lb = 0; lb < bi; ++lb) {
-      float X[NR][4];
-      tmem_ld_rows<NR>(e.d1 + 16 * lb, X);
+      float X[4][4];
+      tc::tmem_ld_quad16(e.acc + 16 * lb, X);
       quad_fma_block(acc, X, Wb + 256 * lb, e.lane, cq);
     }
-    // this block of R = kappa(||x||^2 + ||x_S||^2 - 2 D1) - D2
-    float R[NR][4];
-    {
-      float D1v[NR][4], D2v[NR][4];
-      tmem_ld_rows<NR>(e.d1 + j0, D1v);
-      if (e.nF > 0) {
-        tmem_ld_rows<NR>(e.d2 + j0, D2v);
-      } else {
+    float R[4][4];
+    tc::tmem_ld_quad16(e.acc + j0, R);
 #pragma unroll
-        for (int ri = 0; ri < NR; ++ri)
+    for (int ri = 0; ri < 4; ++ri)
 #pragma unroll
-          for (int cj = 0; cj < 4; ++cj) D2v[ri][cj] = 0.f;
-      }
-      // the kernel map, with the kind resolved outside the loop so that the
-      // 16 evaluations interleave
-      switch (e.kind) {
-        case 0: r_quad<0, NR>(e, j0, D1v, D2v, R); break;
-        case 1: r_quad<1, NR>(e, j0, D1v, D2v, R); break;
-        case 3: r_quad<3, NR>(e, j0, D1v, D2v, R); break;
-        default: r_quad<2, NR>(e, j0, D1v, D2v, R); break;
-      }
-    }
+      for (int cj = 0; cj < 4; ++cj) R[ri][cj] *= (1.f / kAccScale);
     quad_fma_block(acc, R, Wb + 256 * bi, e.lane, cq);
-    float G[NR][4];
+    float G[4][4];
 #pragma unroll
-    for (int ri = 0; ri < NR; ++ri) {
+    for (int ri = 0; ri < 4; ++ri) {
       G[ri][0] = acc[ri][0].x;
       G[ri][1] = acc[ri][0].y;
       G[ri][2] = acc[ri][1].x;
@@ -238,9 +274,9 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
         }
       }
     }
-    tmem_st_rows<NR>(e.d1 + j0, G);  // G_b over the consumed D1 block
+    tc::tmem_st_quad16(e.acc + j0, G);  // G_b over the consumed R block
 #pragma unroll
-    for (int ri = 0; ri < NR; ++ri) {
+    for (int ri = 0; ri < 4; ++ri) {
       if (e.frow[ri]) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
@@ -264,6 +300,34 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
     }
   }
 }
+
+// In-place conversion of one 8-row group of an FP32 F chunk (1 KiB: 8 rows
+// of 32 floats as TMA wrote them, 128-byte swizzle) into the FP16 head and
+// tail of 4096 x: head rows in the group's first 512 bytes, tail rows in the
+// next 512, each an 8-row atom of the 64-byte swizzle.  Lane l takes row
+// l / 4, floats 8 (l % 4) .. 8 (l % 4) + 7; all lanes read before any
+// writes.  Both patterns touch eight distinct 16-byte bank groups per
+// quarter warp.
+__device__ __forceinline__ void convert_group(unsigned char* grp, int lane) {
+  const int i = lane >> 2, q = lane & 3;
+  const float4 a = *(const float4*)(grp + i * 128 + 16 * ((2 * q) ^ i));
+  const float4 b = *(const float4*)(grp + i * 128 + 16 * ((2 * q + 1) ^ i));
+  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float y0 = x[2 * p] * kFScale, y1 = x[2 * p + 1] * kFScale;
+    const __half2 h = __floats2half2_rn(y0, y1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
+    hw[p] = *(const uint32_t*)&h;
+    lw[p] = *(const uint32_t*)&l;
+  }
+  __syncwarp();
+  const int pos = 16 * (q ^ ((i >> 1) & 3));
+  *(uint4*)(grp + i * 64 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *(uint4*)(grp + 512 + i * 64 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
 }  // namespace
 
 struct TcArgs {
@@ -271,30 +335,29 @@ struct TcArgs {
   float* F;
   long long ldF;
   long long N;
-  const float* nrm;     // ||x||^2, FP32
-  const float* nrmS;    // ||x_{S_j}||^2
-  const int* Sacc;      // accepted pivots of the round
-  const float* W;       // blocked-substitution operand of the round (formed by k_prep_tc)
+  const float* nrm;         // ||x||^2, FP32
+  const float* nrmS;        // ||x_{S_j}||^2
+  const int* Sacc;          // accepted pivots of the round
+  const float* W;           // blocked-substitution operand of the round (formed by k_prep_tc)
+  const unsigned char* Bx;  // shared-memory images of the X_S chunks of the round
+  const unsigned char* Bf;  // shared-memory images of the F(S,:) chunks of the round
   double* dvec;
   double* tile_sums;
-  int* err;             // run status word
+  int* err;                 // run status word
   int kind;
   float inv_sigma;
   int xld;
-  const double* L;      // compact FP64 Cholesky factor of the round
+  const double* L;          // compact FP64 Cholesky factor of the round
   int ldL;
-  int d;                // point dimension (round bookkeeping)
-  unsigned* ccnt;       // CTAs done with the round (zero between launches)
+  int d;                    // point dimension (round bookkeeping)
+  unsigned* ccnt;           // CTAs done with the round (zero between launches)
   unsigned long long cond;
   int use_cond;
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_colstep_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmX,
-                 const __grid_constant__ CUtensorMap tmXlo,
-                 const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                 const __grid_constant__ CUtensorMap tmXSh,
-                 const __grid_constant__ CUtensorMap tmXSl, TcArgs a) {
+    k_colstep_tc(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmXh,
+                 const __grid_constant__ CUtensorMap tmXl, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
@@ -308,30 +371,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int s = st->s;
   const long long rank = st->rank;
   const Layout Lo = make_layout(s);
-  const int s_pad = Lo.s_pad, nbox = Lo.nbox, SB = Lo.stage_bytes, NS = Lo.stages;
-  const int nbuf = Lo.nbuf;
-  const int nX = a.xld / kKc;
-  const int nF = (int)((rank + kKc - 1) / kKc);
-  const int nch = nX + nF;
+  const int s_pad = Lo.s_pad, SB = Lo.stage_bytes, NS = Lo.stages, nbuf = Lo.nbuf;
+  const uint32_t bbytes = (uint32_t)Lo.bbytes;
+  const int nXc = a.xld / kXK;
+  const int nF = (int)((rank + kFK - 1) / kFK);
   const long long ntiles = (a.N + kBM - 1) / kBM;
+  const int ntl = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   unsigned char* small = sm + Lo.small_off;
-  int* Ss = (int*)small;                  // [256] pivots of the round (-1 beyond s)
-  float* nrmSs = (float*)(small + 1024);  // [256] their squared norms
+  int* Ss = (int*)small;                       // [256] pivots of the round (-1 beyond s)
+  float* nrmSs = (float*)(small + 1024);       // [256] their squared norms
   uint64_t* full = (uint64_t*)(small + 2048);  // [kMaxStages] A operand landed
-  uint64_t* conv = full + kMaxStages;          // [kMaxStages] A split into head and tail
+  uint64_t* conv = full + kMaxStages;          // [kMaxStages] A ready for the MMAs
   uint64_t* empty = conv + kMaxStages;         // [kMaxStages]
   uint64_t* fullB = empty + kMaxStages;        // [kMaxStages] B operand landed
-  uint64_t* accf = fullB + kMaxStages;         // [2] accumulators of a tile complete
-  uint64_t* tfree = accf + 2;                  // [2] epilogue done with a TMEM buffer
-  uint32_t* tptr = (uint32_t*)(tfree + 2);
+  uint64_t* d1f = fullB + kMaxStages;          // [kMaxBuf] distance MMAs of a tile done
+  uint64_t* midf = d1f + kMaxBuf;              // [kMaxBuf] kappa pass of a tile done
+  uint64_t* accf = midf + kMaxBuf;             // [kMaxBuf] Schur MMAs of a tile done
+  uint64_t* tfree = accf + kMaxBuf;            // [kMaxBuf] epilogue done with a buffer
+  uint32_t* tptr = (uint32_t*)(tfree + kMaxBuf);
   volatile int* abort_flag = (volatile int*)(tptr + 1);
-  volatile int* go_flag = abort_flag + 1;      // [2], one per epilogue group
-  double* red = (double*)(small + 2048 + 512);  // [8]: [group][quarter], or [epilogue warp]
+  volatile int* go_flag = abort_flag + 1;       // [2], one per epilogue group
+  double* red = (double*)(small + 2048 + 768);  // [8]: [group][quarter]
   const float* Wsm = (const float*)(sm + Lo.w_off);
 
-  for (int i = threadIdx.x; i < s_pad; i += kTcThreads) {
+  for (int i = threadIdx.x; i < 256; i += kTcThreads) {
     Ss[i] = i < s ? a.Sacc[i] : -1;
     nrmSs[i] = i < s ? a.nrmS[i] : 0.f;
   }
@@ -345,12 +410,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int i = 0; i < NS; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&fullB[i], 1);
-      tc::mbar_init(&conv[i], 2);   // one arrival per converter warp
+      tc::mbar_init(&conv[i], 2);  // one arrival per converter warp
       tc::mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kMaxBuf; ++i) {
+      tc::mbar_init(&d1f[i], 1);
+      tc::mbar_init(&midf[i], 4);  // one arrival per warp of the tile's epilogue group
       tc::mbar_init(&accf[i], 1);
-      tc::mbar_init(&tfree[i], nbuf == 2 ? 4 : 8);  // one arrival per epilogue warp on the tile
+      tc::mbar_init(&tfree[i], 4);
     }
     *abort_flag = 0;
     tc::fence_mbarrier_init();
@@ -368,61 +435,50 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       tc::prefetch_tmap(&tmF);
-      const uint32_t bbytes = (uint32_t)nbox * (uint32_t)kBoxB;
+      tc::prefetch_tmap(&tmXh);
+      tc::prefetch_tmap(&tmXl);
       // The A operands (rows of F and X, read once per round from HBM) are
       // pulled into L2 kPrefetch chunks ahead of their shared-memory loads,
       // so that a stage turns over at L2 rather than HBM latency.
-      long long ptile = blockIdx.x;
-      int pc = 0;
+      Seq pf;
+      pf.init(ntl, Lo.look, nXc, nF);
       auto prefetch_next = [&]() {
-        if (ptile >= ntiles) return;
-        const int prow = (int)(ptile * kBM);
-        if (pc < nX) {
-          tc::tma_prefetch_2d(&tmX, pc * kKc, prow);
-          tc::tma_prefetch_2d(&tmXlo, pc * kKc, prow);
+        while (!pf.done() && pf.kind() == 2) pf.next();
+        if (pf.done()) return;
+        const int prow = (int)((blockIdx.x + (long long)pf.tile() * gridDim.x) * kBM);
+        if (pf.kind() == 0) {
+          tc::tma_prefetch_2d(&tmXh, pf.c * kXK, prow);
+          tc::tma_prefetch_2d(&tmXl, pf.c * kXK, prow);
         } else {
-          tc::tma_prefetch_2d(&tmF, (nF - 1 - (pc - nX)) * kKc, prow);
+          tc::tma_prefetch_2d(&tmF, pf.c * kFK, prow);
         }
-        if (++pc == nch) {
-          pc = 0;
-          ptile += gridDim.x;
-        }
+        pf.next();
       };
       for (int i = 0; i < kPrefetch; ++i) prefetch_next();
-      long long g = 0;  // chunks issued so far (all tiles)
-      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-        const int row0 = (int)(tile * kBM);
-        for (int c = 0; c < nch; ++c, ++g) {
-          const int stg = (int)(g % NS);
-          if (g >= NS && !tc::mbar_wait_bounded(&empty[stg], (uint32_t)(((g / NS) - 1) & 1),
-                                                kWaitNs, abort_flag))
-            break;
-          unsigned char* sA = sm + stg * SB;
-          unsigned char* sAlo = sA + kStageA;
-          unsigned char* sBh = sA + 2 * kStageA;
-          unsigned char* sBl = sBh + nbox * kBoxB;
-          if (c < nX) {
-            const int x = c * kKc;
-            tc::mbar_arrive_expect_tx(&full[stg], 2u * kStageA);
-            tc::tma_load_2d(sA, &tmX, x, row0, &full[stg]);
-            tc::tma_load_2d(sAlo, &tmXlo, x, row0, &full[stg]);
-            tc::mbar_arrive_expect_tx(&fullB[stg], 2u * bbytes);
-            for (int b = 0; b < nbox; ++b) {
-              tc::tma_load_2d(sBh + b * kBoxB, &tmXSh, x, 64 * b, &fullB[stg]);
-              tc::tma_load_2d(sBl + b * kBoxB, &tmXSl, x, 64 * b, &fullB[stg]);
-            }
-          } else {
-            const int x = (nF - 1 - (c - nX)) * kKc;  // last F column chunk first
-            tc::mbar_arrive_expect_tx(&full[stg], (uint32_t)kStageA);
-            tc::tma_load_2d(sA, &tmF, x, row0, &full[stg]);
-            tc::mbar_arrive_expect_tx(&fullB[stg], 2u * bbytes);
-            for (int b = 0; b < nbox; ++b) {
-              tc::tma_load_2d(sBh + b * kBoxB, &tmBh, x, 64 * b, &fullB[stg]);
-              tc::tma_load_2d(sBl + b * kBoxB, &tmBl, x, 64 * b, &fullB[stg]);
-            }
-          }
-          prefetch_next();
+      long long g = 0;  // stages filled so far
+      Seq sq;
+      for (sq.init(ntl, Lo.look, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
+        const int kd = sq.kind();
+        if (kd == 2) continue;
+        const int stg = (int)(g % NS);
+        if (g >= NS && !tc::mbar_wait_bounded(&empty[stg], (uint32_t)(((g / NS) - 1) & 1),
+                                              kWaitNs, abort_flag))
+          break;
+        const int row0 = (int)((blockIdx.x + (long long)sq.tile() * gridDim.x) * kBM);
+        unsigned char* sA = sm + stg * SB;
+        unsigned char* sB = sA + kStageA;
+        tc::mbar_arrive_expect_tx(&full[stg], (uint32_t)kStageA);
+        tc::mbar_arrive_expect_tx(&fullB[stg], bbytes);
+        if (kd == 0) {
+          tc::tma_load_2d(sA, &tmXh, sq.c * kXK, row0, &full[stg]);
+          tc::tma_load_2d(sA + kStageA / 2, &tmXl, sq.c * kXK, row0, &full[stg]);
+          tc::bulk_load(sB, a.Bx + (size_t)sq.c * bbytes, bbytes, &fullB[stg]);
+        } else {
+          tc::tma_load_2d(sA, &tmF, sq.c * kFK, row0, &full[stg]);
+          tc::bulk_load(sB, a.Bf + (size_t)sq.c * bbytes, bbytes, &fullB[stg]);
         }
+        ++g;
+        prefetch_next();
       }
       if (*abort_flag) {
         // drain: the (at most NS) issued loads not yet consumed must land
@@ -436,107 +492,103 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_tf32(128, (uint32_t)s_pad);
+      const uint32_t id32 = tc::idesc_tf32(128, (uint32_t)s_pad);
+      const uint32_t id16 = tc::idesc_f16(128, (uint32_t)s_pad);
       long long g = 0;
-      int it = 0;
-      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
-        const int buf = it % nbuf;
-        if (it >= nbuf &&
-            !tc::mbar_wait_bounded(&tfree[buf], (uint32_t)(((it / nbuf) - 1) & 1),
-                                   kWaitNs, abort_flag))
+      Seq sq;
+      for (sq.init(ntl, Lo.look, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
+        const int kd = sq.kind(), j = sq.tile(), b = j % nbuf;
+        const uint32_t use = (uint32_t)(j / nbuf);
+        const uint32_t acc = tbase + (uint32_t)(b * Lo.s_alloc);
+        if (kd == 0 && sq.c == 0 && j >= nbuf) {  // the buffer's previous tile is done
+          if (!tc::mbar_wait_bounded(&tfree[b], (use - 1) & 1, kWaitNs, abort_flag)) break;
+          tc::tc_fence_after();
+        }
+        if (kd != 0 && sq.c == 0) {  // kappa(D1) is in the accumulator
+          if (!tc::mbar_wait_bounded(&midf[b], use & 1, kWaitNs, abort_flag)) break;
+          tc::tc_fence_after();
+        }
+        if (kd == 2) {
+          tc::mma_commit(&accf[b]);
+          continue;
+        }
+        const int stg = (int)(g % NS);
+        const uint32_t ph = (uint32_t)((g / NS) & 1);
+        if (!tc::mbar_wait_bounded(&conv[stg], ph, kWaitNs, abort_flag) ||
+            !tc::mbar_wait_bounded(&fullB[stg], ph, kWaitNs, abort_flag))
           break;
         tc::tc_fence_after();
-        const uint32_t d1 = tbase + (uint32_t)(buf * 256);           // D1 of this tile
-        const uint32_t d2 = d1 + (nbuf == 2 ? 128u : 256u);           // D2 of this tile
-        for (int c = 0; c < nch; ++c, ++g) {
-          const int stg = (int)(g % NS);
-          // the A split (which waited only for A) and then B
-          if (!tc::mbar_wait_bounded(&conv[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag) ||
-              !tc::mbar_wait_bounded(&fullB[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag))
-            break;
-          tc::tc_fence_after();
-          const uint32_t aA = tc::smem_u32(sm + stg * SB);
-          const uint32_t aAlo = aA + kStageA;
-          const uint32_t aBh = aA + 2 * kStageA;
-          const uint32_t aBl = aBh + nbox * kBoxB;
-          const uint32_t dt = c < nX ? d1 : d2;
-          const bool first = (c == 0) || (c == nX);
+        const uint32_t aA = tc::smem_u32(sm + stg * SB);
+        const uint32_t aB = aA + kStageA;
+        const uint32_t aBl = aB + 64u * (uint32_t)s_pad;
+        if (kd == 0) {
+          // X head / tail planes (8 KiB each, 64-byte swizzle), TF32, K = 8 per MMA
 #pragma unroll
-          for (int kk = 0; kk < kKc / 8; ++kk) {
-            const uint64_t da = tc::smem_desc_sw128(aA + 32 * kk);
-            const uint64_t dal = tc::smem_desc_sw128(aAlo + 32 * kk);
-            const uint64_t dbh = tc::smem_desc_sw128(aBh + 32 * kk);
-            const uint64_t dbl = tc::smem_desc_sw128(aBl + 32 * kk);
-            // hi.hi and hi.lo share A: the second takes it from the
-            // collector buffer instead of reading shared memory again
-            tc::mma_tf32_keep_a(dt, da, dbh, idesc, (first && kk == 0) ? 0u : 1u);
-            tc::mma_tf32_reuse_a(dt, da, dbl, idesc, 1u);
-            tc::mma_tf32(dt, dal, dbh, idesc, 1u);
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t da = tc::smem_desc(aA + 32 * kk, 512, 4);
+            const uint64_t dal = tc::smem_desc(aA + kStageA / 2 + 32 * kk, 512, 4);
+            const uint64_t dbh = tc::smem_desc(aB + 32 * kk, 512, 4);
+            const uint64_t dbl = tc::smem_desc(aBl + 32 * kk, 512, 4);
+            const uint32_t accum = (sq.c == 0 && kk == 0) ? 0u : 1u;  // a fresh tile starts at 0
+            tc::mma_tf32_keep_a(acc, da, dbh, id32, accum);
+            tc::mma_tf32_reuse_a(acc, da, dbl, id32, 1u);
+            tc::mma_tf32(acc, dal, dbh, id32, 1u);
           }
           tc::mma_commit(&empty[stg]);
+          if (sq.c == nXc - 1) tc::mma_commit(&d1f[b]);
+        } else {
+          // F head / tail in interleaved 512-byte atoms, FP16, K = 16 per MMA
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t da = tc::smem_desc(aA + 32 * kk, 1024, 4);
+            const uint64_t dal = tc::smem_desc(aA + 512 + 32 * kk, 1024, 4);
+            const uint64_t dbh = tc::smem_desc(aB + 32 * kk, 512, 4);
+            const uint64_t dbl = tc::smem_desc(aBl + 32 * kk, 512, 4);
+            tc::mma_f16_keep_a(acc, da, dbh, id16, 1u);
+            tc::mma_f16_reuse_a(acc, da, dbl, id16, 1u);
+            tc::mma_f16(acc, dal, dbh, id16, 1u);
+          }
+          tc::mma_commit(&empty[stg]);
+          if (sq.c == nF - 1) tc::mma_commit(&accf[b]);
         }
-        tc::mma_commit(&accf[it & 1]);
+        ++g;
       }
     }
   } else if (warp < 4) {
-    // ------------------------------------------------ head/tail split of F tiles
-    const int e = threadIdx.x - 64;  // 0..63: rows e and e + 64
+    // ------------------------------------------------ in-place FP16 split of F chunks
+    const int w = warp - 2;
     long long g = 0;
-    for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-      for (int c = 0; c < nch; ++c, ++g) {
-        const int stg = (int)(g % NS);
-        if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g / NS) & 1),
-                                kWaitNs, abort_flag))
-          break;
-        if (c >= nX) {
-          // a row's 128 bytes are one swizzle row: process them in place in
-          // any chunk order (rotated by row to spread the banks); both rows
-          // are read into registers before any store, so that the loads are
-          // not held behind stores the compiler cannot prove apart
-          float4 v[2][8];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = e + 64 * h;
-            const float4* pa = (const float4*)(sm + stg * SB + r * kRowBytes);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[h][q] = pa[(q + r) & 7];
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = e + 64 * h;
-            float4* pa = (float4*)(sm + stg * SB + r * kRowBytes);
-            float4* pl = (float4*)(sm + stg * SB + kStageA + r * kRowBytes);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int j = (q + r) & 7;
-              const float4 x = v[h][q];
-              const float4 hd = make_float4(tc::tf32_head(x.x), tc::tf32_head(x.y),
-                                            tc::tf32_head(x.z), tc::tf32_head(x.w));
-              pa[j] = hd;
-              pl[j] = make_float4(x.x - hd.x, x.y - hd.y, x.z - hd.z, x.w - hd.w);
-            }
-          }
-          tc::fence_proxy_async_smem();
-        }
-        tc::mbar_arrive_warp(&conv[stg]);
+    Seq sq;
+    for (sq.init(ntl, Lo.look, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
+      const int kd = sq.kind();
+      if (kd == 2) continue;
+      const int stg = (int)(g % NS);
+      if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag)) break;
+      if (kd == 1) {
+        unsigned char* sA = sm + stg * SB;
+#pragma unroll 1
+        for (int grp = w; grp < 16; grp += 2) convert_group(sA + 1024 * grp, lane);
+        tc::fence_proxy_async_smem();
       }
+      tc::mbar_arrive_warp(&conv[stg]);
+      ++g;
     }
-  } else if (nbuf == 2) {
-    // ------------------------------------------------ epilogue, two tiles in TMEM:
-    // groups of four warps take alternate tiles
-    const int q = warp & 3;              // TMEM lane quarter of this warp
-    const int grp = (warp - 4) >> 2;     // 0: warps 4-7, 1: warps 8-11
-    const int row = q * 32 + lane;       // tile row = TMEM lane
-    const int gt = row;                  // thread index inside the group
+  } else {
+    // ------------------------------------------------ epilogue: groups of four
+    // warps take alternate tiles
+    const int q = warp & 3;           // TMEM lane quarter of this warp
+    const int grp = (warp - 4) >> 2;  // 0: warps 4-7, 1: warps 8-11
+    const int gt = q * 32 + lane;     // thread index inside the group
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    const int nblk = (s + 15) >> 4;
+    const int nblk = s_pad >> 4;
     const int bar_id = 2 + grp;
-    for (int it = grp;; it += 2) {
-      const long long tile = blockIdx.x + (long long)it * gridDim.x;
-      if (tile >= ntiles) break;
+    const int cq = lane & 3;
+    for (int j = grp; j < ntl; j += 2) {
+      const long long tile = blockIdx.x + (long long)j * gridDim.x;
       const long long row0 = tile * kBM;
+      const int b = j % nbuf;
+      const uint32_t use = (uint32_t)(j / nbuf);
       // this thread's rows: ri -> 32 q + lane / 4 + 16 (ri >> 1) + 8 (ri & 1)
-      const int cq = lane & 3;
       long long growv[4];
       EpiQuad eq;
 #pragma unroll
@@ -544,22 +596,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         growv[ri] = row0 + 32 * q + (lane >> 2) + 16 * (ri >> 1) + 8 * (ri & 1);
         const bool lv = growv[ri] < a.N;
         eq.frow[ri] = lv ? a.F + growv[ri] * a.ldF + rank : nullptr;
-        eq.nr[ri] = lv ? a.nrm[growv[ri]] : 0.f;  // loaded while the accumulators fill
+        eq.nr[ri] = lv ? a.nrm[growv[ri]] : 0.f;
         eq.jpiv[ri] = -1;
       }
       // this thread updates d for row ri = cq (each row once across its quad)
       const long long grow = row0 + 32 * q + (lane >> 2) + 16 * (cq >> 1) + 8 * (cq & 1);
       const bool live = grow < a.N;
       const double dold = live ? a.dvec[grow] : 0.0;
-      for (int j = 0; j < s; ++j) {
-        const long long p = (long long)Ss[j];
+      for (int jj = 0; jj < s; ++jj) {
+        const long long p = (long long)Ss[jj];
 #pragma unroll
         for (int ri = 0; ri < 4; ++ri)
-          if (p == growv[ri]) eq.jpiv[ri] = j;
+          if (p == growv[ri]) eq.jpiv[ri] = jj;
       }
-      tc::mbar_wait_warp(&accf[grp], (uint32_t)((it >> 1) & 1), kWaitNs,
-                         abort_flag);
-      // one thread's reading of the abort flag decides for the whole group
+      eq.acc = tbase + lane_off + (uint32_t)(b * Lo.s_alloc);
+      eq.W = Lo.w_resident ? Wsm : a.W;
+      eq.nrmSs = nrmSs;
+      eq.L = a.L;
+      eq.s = s;
+      eq.kind = a.kind;
+      eq.ldL = a.ldL;
+      eq.cq = cq;
+      eq.lane = lane;
+      eq.even = (rank & 1) == 0;
+      eq.inv_sigma = a.inv_sigma;
+      // ---- the kappa pass, once the tile's distance MMAs are done; one
+      // thread's reading of the abort flag decides for the whole group
+      tc::mbar_wait_warp(&d1f[b], use & 1, kWaitNs, abort_flag);
       asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
       if (gt == 0) go_flag[grp] = *abort_flag ? 0 : 1;
       asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
@@ -568,23 +631,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc::tc_fence_after();
-      eq.d1 = tbase + lane_off + (uint32_t)(grp * 256);
-      eq.d2 = eq.d1 + 128u;
-      eq.W = Lo.w_resident ? Wsm : a.W;
-      eq.nrmSs = nrmSs;
-      eq.L = a.L;
-      eq.s = s;
-      eq.nF = nF;
-      eq.kind = a.kind;
-      eq.ldL = a.ldL;
-      eq.cq = cq;
-      eq.lane = lane;
-      eq.even = (rank & 1) == 0;
-      eq.inv_sigma = a.inv_sigma;
-      float rsq[4] = {0.f, 0.f, 0.f, 0.f}, rc[4] = {0.f, 0.f, 0.f, 0.f};
-      epi_tile_quad<4>(eq, nblk, rsq, rc);
+      switch (eq.kind) {
+        case 0: kappa_pass<0>(eq, nblk); break;
+        case 1: kappa_pass<1>(eq, nblk); break;
+        case 3: kappa_pass<3>(eq, nblk); break;
+        default: kappa_pass<2>(eq, nblk); break;
+      }
       tc::tc_fence_before();
-      tc::mbar_arrive_warp(&tfree[grp]);  // TMEM buffer free for tile it + 2
+      tc::mbar_arrive_warp(&midf[b]);
+      // ---- R complete: substitution, F, d
+      tc::mbar_wait_warp(&accf[b], use & 1, kWaitNs, abort_flag);
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (gt == 0) go_flag[grp] = *abort_flag ? 0 : 1;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (!go_flag[grp]) {
+        if (gt == 0) atomicOr(a.err, (int)kStTimeout);
+        break;
+      }
+      tc::tc_fence_after();
+      float rsq[4] = {0.f, 0.f, 0.f, 0.f}, rc[4] = {0.f, 0.f, 0.f, 0.f};
+      epi_tile_quad(eq, nblk, rsq, rc);
+      tc::tc_fence_before();
+      tc::mbar_arrive_warp(&tfree[b]);  // TMEM buffer free for tile j + nbuf
       // ---- row sums of G^2 across the quad (FP64), residual diagonal, tile sum
       double sq[4];
 #pragma unroll
@@ -607,95 +675,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (gt == 0)
         a.tile_sums[tile] = red[grp * 4] + red[grp * 4 + 1] + red[grp * 4 + 2] + red[grp * 4 + 3];
     }
-  } else {
-    // ------------------------------------------------ epilogue, one tile in TMEM:
-    // all eight warps work on it (groups taking alternate tiles would leave
-    // one idle): warp w takes TMEM lane quarter q = w & 3 (the quarter it
-    // may access) and half h = (w - 4) >> 2 of it, 16 rows, two per thread.
-    const int q = warp & 3;
-    const int h = (warp - 4) >> 2;
-    const int et = (warp - 4) * 32 + lane;  // 0..255
-    const uint32_t lane_off = (uint32_t)(q * 32 + 16 * h) << 16;
-    const int nblk = (s + 15) >> 4;
-    for (int it = 0;; ++it) {
-      const long long tile = blockIdx.x + (long long)it * gridDim.x;
-      if (tile >= ntiles) break;
-      const int buf = it % nbuf;
-      const long long row0 = tile * kBM;
-      // this thread's rows: ri -> 32 q + 16 h + lane / 4 + 8 ri
-      const int cq = lane & 3;
-      long long growv[2];
-      EpiQuad eq;
-#pragma unroll
-      for (int ri = 0; ri < 2; ++ri) {
-        growv[ri] = row0 + 32 * q + 16 * h + (lane >> 2) + 8 * ri;
-        const bool lv = growv[ri] < a.N;
-        eq.frow[ri] = lv ? a.F + growv[ri] * a.ldF + rank : nullptr;
-        eq.nr[ri] = lv ? a.nrm[growv[ri]] : 0.f;  // loaded while the accumulators fill
-        eq.jpiv[ri] = -1;
-      }
-      // threads cq = 0, 1 of a quad update d for rows ri = cq
-      const long long grow = row0 + 32 * q + 16 * h + (lane >> 2) + 8 * (cq & 1);
-      const bool live = cq < 2 && grow < a.N;
-      const double dold = live ? a.dvec[grow] : 0.0;
-      for (int j = 0; j < s; ++j) {
-        const long long p = (long long)Ss[j];
-#pragma unroll
-        for (int ri = 0; ri < 2; ++ri)
-          if (p == growv[ri]) eq.jpiv[ri] = j;
-      }
-      tc::mbar_wait_warp(&accf[it & 1], (uint32_t)((it >> 1) & 1), kWaitNs, abort_flag);
-      // one thread's reading of the abort flag decides for all eight warps
-      asm volatile("bar.sync 2, 256;" ::: "memory");
-      if (et == 0) go_flag[0] = *abort_flag ? 0 : 1;
-      asm volatile("bar.sync 2, 256;" ::: "memory");
-      if (!go_flag[0]) {
-        if (et == 0) atomicOr(a.err, (int)kStTimeout);
-        break;
-      }
-      tc::tc_fence_after();
-      eq.d1 = tbase + lane_off + (uint32_t)(buf * 256);
-      eq.d2 = eq.d1 + (nbuf == 2 ? 128u : 256u);
-      eq.W = Lo.w_resident ? Wsm : a.W;
-      eq.nrmSs = nrmSs;
-      eq.L = a.L;
-      eq.s = s;
-      eq.nF = nF;
-      eq.kind = a.kind;
-      eq.ldL = a.ldL;
-      eq.cq = cq;
-      eq.lane = lane;
-      eq.even = (rank & 1) == 0;
-      eq.inv_sigma = a.inv_sigma;
-      float rsq[2] = {0.f, 0.f}, rc[2] = {0.f, 0.f};
-      epi_tile_quad<2>(eq, nblk, rsq, rc);
-      tc::tc_fence_before();
-      tc::mbar_arrive_warp(&tfree[buf]);  // TMEM buffer free for tile it + nbuf
-      // ---- row sums of G^2 across the quad (FP64), residual diagonal, tile sum
-      double sq[2];
-#pragma unroll
-      for (int ri = 0; ri < 2; ++ri) {
-        sq[ri] = (double)rsq[ri] - (double)rc[ri];
-        sq[ri] += __shfl_xor_sync(0xffffffffu, sq[ri], 1);
-        sq[ri] += __shfl_xor_sync(0xffffffffu, sq[ri], 2);
-      }
-      const double mysq = (cq & 1) == 0 ? sq[0] : sq[1];
-      const int myjp = (cq & 1) == 0 ? eq.jpiv[0] : eq.jpiv[1];
-      double dn = 0.0;
-      if (live) {
-        const double v = dold - mysq;
-        dn = (v > 0.0 && myjp < 0) ? v : 0.0;
-        a.dvec[grow] = dn;
-      }
-      for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
-      if (lane == 0) red[warp - 4] = dn;
-      asm volatile("bar.sync 2, 256;" ::: "memory");
-      if (et == 0) {
-        double ts = 0.0;
-        for (int w = 0; w < 8; ++w) ts += red[w];
-        a.tile_sums[tile] = ts;
-      }
-    }
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -705,8 +684,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (atomicAdd(a.ccnt, 1u) == gridDim.x - 1) {
       __threadfence();
       // three split products per K step, M = 128 rows per tile, N = s_pad
-      const double mma = 6.0 * 128.0 * (double)ntiles * (double)s_pad * (double)(nch * kKc);
-      round_end_body(st, a.cond, a.use_cond, a.N, a.d, 4, mma, 0.0);
+      const double per = 6.0 * 128.0 * (double)ntiles * (double)s_pad;
+      round_end_body(st, a.cond, a.use_cond, a.N, a.d, 4, per * (double)a.xld,
+                     per * (double)(nF * kFK));
       *a.ccnt = 0u;
     }
   }
@@ -730,6 +710,8 @@ cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, unsigned lon
   a.nrmS = m.nrmS;
   a.Sacc = b.Sacc;
   a.W = m.Linv32;
+  a.Bx = m.Bx;
+  a.Bf = m.Bf;
   a.dvec = b.dvec;
   a.tile_sums = b.tile_sums;
   a.err = m.err;
@@ -746,7 +728,7 @@ cudaError_t launch_colstep_tc(const TcMaps& m, const DevBuffers& b, unsigned lon
   const unsigned grid = (unsigned)(ntiles < m.num_sms ? ntiles : m.num_sms);
   // the shared-memory layout depends on s, which only the device knows: the
   // launch reserves the maximum
-  k_colstep_tc<<<grid, kTcThreads, kSmemMax, s>>>(m.F, m.X, m.Xlo, m.FSh, m.FSl, m.XSh, m.XSl, a);
+  k_colstep_tc<<<grid, kTcThreads, kSmemMax, s>>>(m.F, m.Xh, m.Xl, a);
   return cudaGetLastError();
 }
 

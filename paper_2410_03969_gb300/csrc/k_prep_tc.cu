@@ -1,14 +1,20 @@
 // Per-round operand preparation for the tensor-core column step (mixed
 // mode), Algorithm 2 step 3 of arXiv 2410.03969:
-//   - rows j < s of the B operands: F(S_j, 0:rank) and x_{S_j}, each split
-//     into TF32 head and tail planes; rows [s, 64 * ceil(s_pad / 64)) and the
-//     columns [rank, 32 * ceil(rank / 32)) are zero so that padded MMA
-//     columns and padded K chunks contribute nothing;
+//   - the B operands of the round as the exact shared-memory images the
+//     column step's MMAs read, one contiguous image per K chunk (loaded with
+//     one bulk copy): for chunk c of the Schur part, rows j < s_pad of
+//     [head | tail] of -4096 F(S_j, 32 c .. 32 c + 31) in FP16 (64-byte rows,
+//     64-byte swizzle); for chunk c of the distance part, rows j < s_pad of
+//     [head | tail] of x_{S_j}(16 c .. 16 c + 15) as TF32 planes (64-byte
+//     rows, 64-byte swizzle).  Rows j >= s and columns >= rank are zero, so
+//     padded MMA columns and the columns of F not yet formed contribute
+//     nothing;
 //   - ||x_{S_j}||^2;
 //   - the blocked-substitution operand W built from the round's compact
 //     Cholesky factor L in FP64 and rounded once to FP32 (wblk below), in
 //     the same launch.
-// Also the one-time split of X into head and tail planes.
+// Also the one-time split of X into TF32 head and tail planes.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -16,51 +22,61 @@
 
 namespace rpchol {
 
-// Row j of the B operands (one CTA per row).
+// Byte offset of the 16-byte piece q (0..3) of row j in a 64-byte-row image
+// with the 64-byte swizzle (piece q of row j sits at q ^ ((j >> 1) & 3)).
+__device__ __forceinline__ int sw64_off(int j, int q) { return j * 64 + 16 * (q ^ ((j >> 1) & 3)); }
+
+// Row j of the B images (one CTA per row).
 __device__ __forceinline__ void prep_row(const DevState* st, const float* __restrict__ F,
                                          long long ldF, const float* __restrict__ X, int xld,
                                          const float* __restrict__ nrm,
-                                         const int* __restrict__ Sacc, float* FSh, float* FSl,
-                                         float* XSh, float* XSl, float* nrmS, int j) {
+                                         const int* __restrict__ Sacc, unsigned char* Bf,
+                                         unsigned char* Bx, float* nrmS, int j) {
   const int s = st->s;
   if (s == 0) return;
   const long long rank = st->rank;
-  const long long kpad = (rank + 31) & ~31ll;
   const int s_pad = (s + 15) & ~15;
-  const int rows = (s_pad + 63) & ~63;
-  if (j >= rows) return;
-  float* fh = FSh + (long long)j * ldF;
-  float* fl = FSl + (long long)j * ldF;
-  float* xh = XSh + (long long)j * xld;
-  float* xl = XSl + (long long)j * xld;
-  if (j < s) {
-    const int p = Sacc[j];
-    const float* src = F + (long long)p * ldF;
-    for (long long m = threadIdx.x; m < kpad; m += blockDim.x) {
-      const float v = m < rank ? src[m] : 0.f;
-      const float h = tc::tf32_head(v);
-      fh[m] = h;
-      fl[m] = v - h;
+  if (j >= s_pad) return;
+  const size_t cb = 128 * (size_t)s_pad;  // bytes of one chunk image
+  const int nF = (int)((rank + 31) >> 5);
+  const int nXc = xld >> 4;
+  const int p = j < s ? Sacc[j] : -1;
+  const float* frow = p >= 0 ? F + (long long)p * ldF : nullptr;
+  const float* xrow = p >= 0 ? X + (long long)p * xld : nullptr;
+  for (int it = threadIdx.x; it < 4 * nF; it += blockDim.x) {
+    const int c = it >> 2, q = it & 3;
+    const long long col = 32ll * c + 8 * q;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = (frow && col + e < rank) ? -4096.f * frow[col + e] : 0.f;
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __half2 h = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+      const float2 hf = __half22float2(h);
+      const __half2 l = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+      hw[e] = *(const uint32_t*)&h;
+      lw[e] = *(const uint32_t*)&l;
     }
-    const float* xs = X + (long long)p * xld;
-    for (int l = threadIdx.x; l < xld; l += blockDim.x) {
-      const float v = xs[l];
-      const float h = tc::tf32_head(v);
-      xh[l] = h;
-      xl[l] = v - h;
-    }
-    if (threadIdx.x == 0) nrmS[j] = nrm[p];
-  } else {
-    for (long long m = threadIdx.x; m < kpad; m += blockDim.x) {
-      fh[m] = 0.f;
-      fl[m] = 0.f;
-    }
-    for (int l = threadIdx.x; l < xld; l += blockDim.x) {
-      xh[l] = 0.f;
-      xl[l] = 0.f;
-    }
-    if (threadIdx.x == 0) nrmS[j] = 0.f;
+    unsigned char* base = Bf + (size_t)c * cb + sw64_off(j, q);
+    *(uint4*)base = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *(uint4*)(base + 64 * s_pad) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
+  for (int it = threadIdx.x; it < 4 * nXc; it += blockDim.x) {
+    const int c = it >> 2, q = it & 3;
+    const int col = 16 * c + 4 * q;
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float v = xrow ? xrow[col + e] : 0.f;
+      h[e] = tc::tf32_head(v);
+      l[e] = v - h[e];
+    }
+    unsigned char* base = Bx + (size_t)c * cb + sw64_off(j, q);
+    *(float4*)base = make_float4(h[0], h[1], h[2], h[3]);
+    *(float4*)(base + 64 * s_pad) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+  if (threadIdx.x == 0) nrmS[j] = p >= 0 ? nrm[p] : 0.f;
 }
 
 // Blocked forward substitution operand for G L^* = R.  With the columns in
@@ -129,12 +145,12 @@ constexpr int kWParts = 8;
 __global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float* __restrict__ F,
                                                  long long ldF, const float* __restrict__ X,
                                                  int xld, const float* __restrict__ nrm,
-                                                 const int* __restrict__ Sacc, float* FSh,
-                                                 float* FSl, float* XSh, float* XSl, float* nrmS,
+                                                 const int* __restrict__ Sacc, unsigned char* Bf,
+                                                 unsigned char* Bx, float* nrmS,
                                                  const double* __restrict__ L, int ldL, float* W) {
   if (st->done) return;
   if (blockIdx.x < kTMax) {
-    prep_row(st, F, ldF, X, xld, nrm, Sacc, FSh, FSl, XSh, XSl, nrmS, (int)blockIdx.x);
+    prep_row(st, F, ldF, X, xld, nrm, Sacc, Bf, Bx, nrmS, (int)blockIdx.x);
   } else {
     const int i = (int)blockIdx.x - kTMax;
     wblk(st, L, ldL, W, i / kWParts, i % kWParts, kWParts);
@@ -152,8 +168,8 @@ __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, f
 
 cudaError_t launch_prep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
   k_prep_tc<<<kTMax + kWParts * (kTMax / 16), 256, 0, s>>>(
-      b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc, m.FShp, m.FSlp, m.XShp, m.XSlp,
-      m.nrmS, b.L, b.Tmax, m.Linv32);
+      b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc, m.Bf, m.Bx, m.nrmS, b.L, b.Tmax,
+      m.Linv32);
   return cudaGetLastError();
 }
 

@@ -156,9 +156,10 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D fp32 map over a row-major (rows x inner) array with leading dimension
-// `inner`, box 32 (128 bytes) x box_rows, 128-byte swizzle, zero fill.
+// `inner`, box box_inner x box_rows, the given swizzle, zero fill.
 rpchol_status make_map(CUtensorMap* m, const void* base, unsigned long long inner,
-                       unsigned long long rows, unsigned box_rows) {
+                       unsigned long long rows, unsigned box_inner, unsigned box_rows,
+                       CUtensorMapSwizzle swz) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) {
     set_err("cuTensorMapEncodeTiled is unavailable");
@@ -166,10 +167,10 @@ rpchol_status make_map(CUtensorMap* m, const void* base, unsigned long long inne
   }
   cuuint64_t dims[2] = {inner, rows};
   cuuint64_t strides[1] = {inner * 4ull};
-  cuuint32_t box[2] = {32u, box_rows};
+  cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1u, 1u};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
-                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_err("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -551,43 +552,35 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   if (c->use_tc) {
     TcMaps& m = c->tc;
     const size_t xbytes = sizeof(float) * (size_t)N * b.xld;
-    const size_t fsbytes = sizeof(float) * (size_t)kTMax * b.ldF;
-    const size_t xsbytes = sizeof(float) * (size_t)kTMax * b.xld;
+    // one 128 x kTMax-byte image per K chunk: ldF / 32 chunks of F(S,:), xld / 16 of X_S
+    const size_t bfbytes = (size_t)(b.ldF / 32) * 128 * kTMax;
+    const size_t bxbytes = (size_t)(b.xld / 16) * 128 * kTMax;
     void* q;
     if ((rs = dev_alloc(c, &q, xbytes)) != RPCHOL_OK) return fail(rs);
     m.Xhp = (float*)q;
     if ((rs = dev_alloc(c, &q, xbytes)) != RPCHOL_OK) return fail(rs);
     m.Xlp = (float*)q;
-    if ((rs = dev_alloc(c, &q, fsbytes)) != RPCHOL_OK) return fail(rs);
-    m.FShp = (float*)q;
-    if ((rs = dev_alloc(c, &q, fsbytes)) != RPCHOL_OK) return fail(rs);
-    m.FSlp = (float*)q;
-    if ((rs = dev_alloc(c, &q, xsbytes)) != RPCHOL_OK) return fail(rs);
-    m.XShp = (float*)q;
-    if ((rs = dev_alloc(c, &q, xsbytes)) != RPCHOL_OK) return fail(rs);
-    m.XSlp = (float*)q;
+    if ((rs = dev_alloc(c, &q, bfbytes)) != RPCHOL_OK) return fail(rs);
+    m.Bf = (unsigned char*)q;
+    if ((rs = dev_alloc(c, &q, bxbytes)) != RPCHOL_OK) return fail(rs);
+    m.Bx = (unsigned char*)q;
     if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax)) != RPCHOL_OK) return fail(rs);
     m.nrmS = (float*)q;
     if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax * kTMax)) != RPCHOL_OK) return fail(rs);
     m.Linv32 = (float*)q;
-    if ((rs = dev_alloc(c, &q, sizeof(float) * kTMax)) != RPCHOL_OK) return fail(rs);
-    m.invd = (float*)q;
     m.err = (int*)((char*)b.st + offsetof(DevState, status));
     m.num_sms = b.num_sms;
-    e = cudaMemsetAsync(m.FShp, 0, fsbytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m.FSlp, 0, fsbytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m.XShp, 0, xsbytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m.XSlp, 0, xsbytes, c->stream);
+    e = cudaMemsetAsync(m.Bf, 0, bfbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.Bx, 0, bxbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.Linv32, 0, sizeof(float) * kTMax * kTMax, c->stream);
     if (e == cudaSuccess) e = launch_split_x(m, b, c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "tensor-core operand setup"));
-    if ((rs = make_map(&m.F, b.F, b.ldF, N, 128)) != RPCHOL_OK) return fail(rs);
-    if ((rs = make_map(&m.X, m.Xhp, b.xld, N, 128)) != RPCHOL_OK) return fail(rs);
-    if ((rs = make_map(&m.Xlo, m.Xlp, b.xld, N, 128)) != RPCHOL_OK) return fail(rs);
-    if ((rs = make_map(&m.FSh, m.FShp, b.ldF, kTMax, 64)) != RPCHOL_OK) return fail(rs);
-    if ((rs = make_map(&m.FSl, m.FSlp, b.ldF, kTMax, 64)) != RPCHOL_OK) return fail(rs);
-    if ((rs = make_map(&m.XSh, m.XShp, b.xld, kTMax, 64)) != RPCHOL_OK) return fail(rs);
-    if ((rs = make_map(&m.XSl, m.XSlp, b.xld, kTMax, 64)) != RPCHOL_OK) return fail(rs);
+    if ((rs = make_map(&m.F, b.F, b.ldF, N, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B)) != RPCHOL_OK)
+      return fail(rs);
+    if ((rs = make_map(&m.Xh, m.Xhp, b.xld, N, 16, 128, CU_TENSOR_MAP_SWIZZLE_64B)) != RPCHOL_OK)
+      return fail(rs);
+    if ((rs = make_map(&m.Xl, m.Xlp, b.xld, N, 16, 128, CU_TENSOR_MAP_SWIZZLE_64B)) != RPCHOL_OK)
+      return fail(rs);
   }
   e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(cuda_fail(e, "create"));
@@ -1007,8 +1000,8 @@ int64_t rpchol_context_bytes(int64_t N, int32_t d, int64_t k_max, int32_t T_max,
   b += 8LL * T_max * (ldF + kTMax);                   // extended operand rows
   if (mixed && N >= 128) {
     b += 2 * 4 * N * xld;                             // TF32 planes of X
-    b += 2 * 4LL * kTMax * ldF + 2 * 4LL * kTMax * xld;  // planes of F(S,:), X_S
-    b += 4LL * kTMax + 4LL * kTMax * kTMax + 4LL * kTMax;
+    b += (ldF / 32) * 128LL * kTMax + (xld / 16) * 128LL * kTMax;  // chunk images of F(S,:), X_S
+    b += 4LL * kTMax + 4LL * kTMax * kTMax;
   }
   return (int64_t)b;
 }
