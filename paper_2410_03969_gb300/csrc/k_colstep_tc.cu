@@ -45,10 +45,10 @@
 // columns of F (FP32 by TMA, converted in place into 64-byte-swizzled FP16
 // head and tail) against the same 32 of F(S,:).  The B operands of the
 // round are laid out by the operand-prep kernel as the exact shared-memory
-// image of each chunk and arrive with one bulk copy per chunk.  When TMEM
-// holds three or more tiles the producer streams a tile's X chunks one tile
-// ahead of its F chunks, so that the kappa pass of the next tile runs while
-// the current tile's Schur MMAs execute.  Every wait is bounded: on expiry
+// image of each chunk and arrive with one bulk copy per chunk.  The
+// producer streams the next tile's X chunks inside the current tile's F
+// chunks (see Seq), so that the next tile's distances and kappa pass run
+// while the current tile's Schur MMAs execute.  Every wait is bounded: on expiry
 // the CTA raises the timeout bit of the run status, drains its own copies
 // and frees its TMEM.
 #include <cuda.h>
@@ -76,8 +76,7 @@ constexpr float kAccScale = 16777216.f;   // 4096^2: the scale of the Schur prod
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 struct Layout {
-  int s_pad, s_alloc, nbuf, look, bbytes, stage_bytes, stages, w_resident, w_off, small_off,
-      total;
+  int s_pad, s_alloc, nbuf, bbytes, stage_bytes, stages, w_resident, w_off, small_off, total;
 };
 
 // Stages first, then (if room is left for at least as many stages as
@@ -88,7 +87,6 @@ __host__ __device__ inline Layout make_layout(int s) {
   L.s_alloc = (L.s_pad + 31) & ~31;
   L.nbuf = 512 / L.s_alloc;
   if (L.nbuf > kMaxBuf) L.nbuf = kMaxBuf;
-  L.look = L.nbuf >= 3 ? 1 : 0;
   L.bbytes = 128 * L.s_pad;
   L.stage_bytes = kStageA + L.bbytes;
   const int nblk = L.s_pad >> 4;
@@ -107,36 +105,46 @@ __host__ __device__ inline Layout make_layout(int s) {
   return L;
 }
 
-// The chunk sequence a CTA streams: for t = 0, 1, ...: the X chunks of
-// local tile t (if t < ntl), then the F chunks of local tile t - look (if
-// t >= look).  A tile whose round has no F columns yet (rank 0) gets one
-// empty F item (kind 2), which loads nothing.  Producer, converter and MMA
-// issuer walk the same sequence.
+// The chunk sequence a CTA streams: the X chunks of local tile 0, then for
+// each local tile t its F chunks with the X chunks of tile t + 1 inserted
+// after the first `split` of them.  A tile whose round has no F columns yet
+// (rank 0) gets one empty F item (kind 2), which loads nothing.  With three
+// or more tiles in TMEM split = 0 (the next tile's distances and kappa pass
+// run while this tile's Schur MMAs execute); with two, the next tile's
+// buffer frees only when the epilogue of tile t - 1 is done, so its X chunks
+// come two thirds of the way through tile t's F chunks.  Producer, converter
+// and MMA issuer walk the same sequence.
 struct Seq {
-  int t, ph, c;
-  int ntl, look, nXc, nF;
-  __device__ void init(int ntl_, int look_, int nXc_, int nF_) {
+  int t, ph, c;  // ph 0: F(t) before the split, 1: X(t + 1), 2: F(t) after it
+  int ntl, nXc, nF, nFi, split;
+  __device__ void init(int ntl_, int nbuf, int nXc_, int nF_) {
     ntl = ntl_;
-    look = look_;
     nXc = nXc_;
     nF = nF_;
-    t = 0;
+    nFi = nF > 0 ? nF : 1;
+    split = nbuf >= 3 ? 0 : (2 * nFi) / 3;
+    t = -1;
     ph = 0;
     c = 0;
     settle();
   }
-  __device__ bool done() const { return t >= ntl + look; }
-  __device__ int kind() const { return ph == 0 ? 0 : (nF > 0 ? 1 : 2); }
-  __device__ int tile() const { return ph == 0 ? t : t - look; }
+  __device__ bool done() const { return t >= ntl; }
+  __device__ int kind() const { return ph == 1 ? 0 : (nF > 0 ? 1 : 2); }
+  __device__ int tile() const { return ph == 1 ? t + 1 : t; }
   __device__ void settle() {
     for (;;) {
-      if (t >= ntl + look) return;
+      if (t >= ntl) return;
       if (ph == 0) {
-        if (t < ntl && c < nXc) return;
+        if (t >= 0 && c < split) return;
         ph = 1;
         c = 0;
       }
-      if (t - look >= 0 && c < (nF > 0 ? nF : 1)) return;
+      if (ph == 1) {
+        if (t + 1 < ntl && c < nXc) return;
+        ph = 2;
+        c = t >= 0 ? split : 0;
+      }
+      if (t >= 0 && c < nFi) return;
       ph = 0;
       c = 0;
       ++t;
@@ -188,12 +196,13 @@ __device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float 
 // The kernel map of the epilogue in FP32 with the fast exponential
 // intrinsic: its error bound (2 + 1.16 |x|) ulp of exp(x) is an absolute
 // error below 1e-7 for every kernel value in (0, 1], the size of the FP32
-// rounding of the values it enters.
+// rounding of the values it enters; r = r^2 rsqrt(r^2) adds at most a few
+// ulp to r.
 template <int KIND>
 __device__ __forceinline__ float phi_fast(float inv_sigma, float r2) {
   r2 = r2 > 0.f ? r2 : 0.f;
   if (KIND == 0) return __expf(-0.5f * r2 * inv_sigma * inv_sigma);
-  const float r = sqrtf(r2);
+  const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
   if (KIND == 1) return __expf(-r * inv_sigma);
   if (KIND == 3) {
     const float t = 1.7320508075688772f * r * inv_sigma;
@@ -205,25 +214,39 @@ __device__ __forceinline__ float phi_fast(float inv_sigma, float r2) {
 
 // The kappa pass: D1 -> 4096^2 kappa(||x||^2 + ||x_S||^2 - 2 D1) in place,
 // columns beyond s zero, kappa(x, x) = 1 at a row's own pivot column.
+// Blocks are loaded two at a time and stored without waiting; one wait at
+// the end covers every store.
+template <int KIND>
+__device__ __forceinline__ void kappa_block(const EpiQuad& e, int j0, const float (&D1v)[4][4]) {
+  float K[4][4];
+#pragma unroll
+  for (int cj = 0; cj < 4; ++cj) {
+    const int col = j0 + 8 * (cj >> 1) + 2 * e.cq + (cj & 1);
+    const float ns = e.nrmSs[col];
+#pragma unroll
+    for (int ri = 0; ri < 4; ++ri) {
+      const float kv =
+          col == e.jpiv[ri] ? 1.f : phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
+      K[ri][cj] = col < e.s ? kv * kAccScale : 0.f;
+    }
+  }
+  tc::tmem_st_quad16_nowait(e.acc + j0, K);
+}
+
 template <int KIND>
 __device__ __forceinline__ void kappa_pass(const EpiQuad& e, int nblk) {
-  for (int bi = 0; bi < nblk; ++bi) {
-    const int j0 = 16 * bi;
-    float D1v[4][4], K[4][4];
-    tc::tmem_ld_quad16(e.acc + j0, D1v);
-#pragma unroll
-    for (int cj = 0; cj < 4; ++cj) {
-      const int col = j0 + 8 * (cj >> 1) + 2 * e.cq + (cj & 1);
-      const float ns = e.nrmSs[col];
-#pragma unroll
-      for (int ri = 0; ri < 4; ++ri) {
-        const float kv =
-            col == e.jpiv[ri] ? 1.f : phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
-        K[ri][cj] = col < e.s ? kv * kAccScale : 0.f;
-      }
+  for (int bi = 0; bi < nblk; bi += 2) {
+    float D0[4][4], D1[4][4];
+    if (bi + 1 < nblk) {
+      tc::tmem_ld_quad16x2(e.acc + 16 * bi, e.acc + 16 * (bi + 1), D0, D1);
+      kappa_block<KIND>(e, 16 * bi, D0);
+      kappa_block<KIND>(e, 16 * (bi + 1), D1);
+    } else {
+      tc::tmem_ld_quad16(e.acc + 16 * bi, D0);
+      kappa_block<KIND>(e, 16 * bi, D0);
     }
-    tc::tmem_st_quad16(e.acc + j0, K);
   }
+  tc::tmem_wait_st();
 }
 
 // G L^* = R by blocks of 16 columns in the quad layout; R is the
@@ -301,32 +324,42 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
   }
 }
 
-// In-place conversion of one 8-row group of an FP32 F chunk (1 KiB: 8 rows
-// of 32 floats as TMA wrote them, 128-byte swizzle) into the FP16 head and
-// tail of 4096 x: head rows in the group's first 512 bytes, tail rows in the
-// next 512, each an 8-row atom of the 64-byte swizzle.  Lane l takes row
-// l / 4, floats 8 (l % 4) .. 8 (l % 4) + 7; all lanes read before any
-// writes.  Both patterns touch eight distinct 16-byte bank groups per
-// quarter warp.
-__device__ __forceinline__ void convert_group(unsigned char* grp, int lane) {
+// In-place conversion of an FP32 F chunk (16 KiB: 128 rows of 32 floats as
+// TMA wrote them, 128-byte swizzle) into the FP16 head and tail of 4096 x.
+// Each 8-row group g (1 KiB at 1024 g) becomes its head rows (the first 512
+// bytes) and tail rows (the next 512), each an 8-row atom of the 64-byte
+// swizzle.  Warp w takes groups w, w + 2, ..., w + 14; lane l takes row
+// l / 4 of a group, floats 8 (l % 4) .. 8 (l % 4) + 7.  All eight groups are
+// read before any write (the reads and writes of a group overlap in place).
+// Both patterns touch eight distinct 16-byte bank groups per quarter warp.
+__device__ __forceinline__ void convert_chunk(unsigned char* sA, int w, int lane) {
   const int i = lane >> 2, q = lane & 3;
-  const float4 a = *(const float4*)(grp + i * 128 + 16 * ((2 * q) ^ i));
-  const float4 b = *(const float4*)(grp + i * 128 + 16 * ((2 * q + 1) ^ i));
-  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-  uint32_t hw[4], lw[4];
+  float4 va[8], vb[8];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const float y0 = x[2 * p] * kFScale, y1 = x[2 * p + 1] * kFScale;
-    const __half2 h = __floats2half2_rn(y0, y1);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
-    hw[p] = *(const uint32_t*)&h;
-    lw[p] = *(const uint32_t*)&l;
+  for (int u = 0; u < 8; ++u) {
+    const unsigned char* grp = sA + 1024 * (w + 2 * u);
+    va[u] = *(const float4*)(grp + i * 128 + 16 * ((2 * q) ^ i));
+    vb[u] = *(const float4*)(grp + i * 128 + 16 * ((2 * q + 1) ^ i));
   }
   __syncwarp();
   const int pos = 16 * (q ^ ((i >> 1) & 3));
-  *(uint4*)(grp + i * 64 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-  *(uint4*)(grp + 512 + i * 64 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const float x[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float y0 = x[2 * p] * kFScale, y1 = x[2 * p + 1] * kFScale;
+      const __half2 h = __floats2half2_rn(y0, y1);
+      const float2 hf = __half22float2(h);
+      const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
+      hw[p] = *(const uint32_t*)&h;
+      lw[p] = *(const uint32_t*)&l;
+    }
+    unsigned char* grp = sA + 1024 * (w + 2 * u);
+    *(uint4*)(grp + i * 64 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *(uint4*)(grp + 512 + i * 64 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
 }
 }  // namespace
 
@@ -441,7 +474,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // pulled into L2 kPrefetch chunks ahead of their shared-memory loads,
       // so that a stage turns over at L2 rather than HBM latency.
       Seq pf;
-      pf.init(ntl, Lo.look, nXc, nF);
+      pf.init(ntl, nbuf, nXc, nF);
       auto prefetch_next = [&]() {
         while (!pf.done() && pf.kind() == 2) pf.next();
         if (pf.done()) return;
@@ -457,7 +490,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < kPrefetch; ++i) prefetch_next();
       long long g = 0;  // stages filled so far
       Seq sq;
-      for (sq.init(ntl, Lo.look, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
+      for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
         const int kd = sq.kind();
         if (kd == 2) continue;
         const int stg = (int)(g % NS);
@@ -496,7 +529,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t id16 = tc::idesc_f16(128, (uint32_t)s_pad);
       long long g = 0;
       Seq sq;
-      for (sq.init(ntl, Lo.look, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
+      for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
         const int kd = sq.kind(), j = sq.tile(), b = j % nbuf;
         const uint32_t use = (uint32_t)(j / nbuf);
         const uint32_t acc = tbase + (uint32_t)(b * Lo.s_alloc);
@@ -559,15 +592,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int w = warp - 2;
     long long g = 0;
     Seq sq;
-    for (sq.init(ntl, Lo.look, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
+    for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
       const int kd = sq.kind();
       if (kd == 2) continue;
       const int stg = (int)(g % NS);
       if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag)) break;
       if (kd == 1) {
         unsigned char* sA = sm + stg * SB;
-#pragma unroll 1
-        for (int grp = w; grp < 16; grp += 2) convert_group(sA + 1024 * grp, lane);
+        convert_chunk(sA, w, lane);
         tc::fence_proxy_async_smem();
       }
       tc::mbar_arrive_warp(&conv[stg]);

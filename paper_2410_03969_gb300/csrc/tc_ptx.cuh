@@ -361,6 +361,21 @@ __device__ __forceinline__ void tmem_st16_sync(uint32_t taddr, const float* v) {
       : "memory");
 }
 
+// 16 consecutive 32-bit columns of this thread's TMEM lane stored, without
+// the wait (see tmem_wait_st).
+__device__ __forceinline__ void tmem_st16_nowait(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
 // 16x256b accesses: in a 16-lane half of the warp's lane quarter, thread t
 // holds lanes t/4 and t/4 + 8, columns 2(t%4) and 2(t%4) + 1 of an 8-column
 // group.  The quad form below covers a warp's 32 lanes and 16 columns
@@ -412,6 +427,69 @@ __device__ __forceinline__ void tmem_st_quad16(uint32_t ta, const float (&v)[4][
       "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
       "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
+}
+
+// Two blocks of the quad form (two TMEM addresses), eight loads and one wait.
+__device__ __forceinline__ void tmem_ld_quad16x2(uint32_t ta, uint32_t tb, float (&va)[4][4],
+                                                 float (&vb)[4][4]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0, %1, %2, %3}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%4, %5, %6, %7}, [%33];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%8, %9, %10, %11}, [%34];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%12, %13, %14, %15}, [%35];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%16, %17, %18, %19}, [%36];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%20, %21, %22, %23}, [%37];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%24, %25, %26, %27}, [%38];\n\t"
+      "tcgen05.ld.sync.aligned.16x256b.x1.b32 {%28, %29, %30, %31}, [%39];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(ta), "r"(ta + 8u), "r"(ta + (16u << 16)), "r"(ta + (16u << 16) + 8u), "r"(tb),
+        "r"(tb + 8u), "r"(tb + (16u << 16)), "r"(tb + (16u << 16) + 8u)
+      : "memory");
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          va[2 * h + i][2 * g + e] = __uint_as_float(r[4 * (2 * h + g) + 2 * i + e]);
+          vb[2 * h + i][2 * g + e] = __uint_as_float(r[16 + 4 * (2 * h + g) + 2 * i + e]);
+        }
+}
+
+// The quad-form store without its wait: the caller issues tmem_wait_st()
+// before anything that must see the stored values.
+__device__ __forceinline__ void tmem_st_quad16_nowait(uint32_t ta, const float (&v)[4][4]) {
+  uint32_t r[16];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) r[4 * (2 * h + g) + 2 * i + e] = __float_as_uint(v[2 * h + i][2 * g + e]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%0], {%4, %5, %6, %7};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%1], {%8, %9, %10, %11};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%2], {%12, %13, %14, %15};\n\t"
+      "tcgen05.st.sync.aligned.16x256b.x1.b32 [%3], {%16, %17, %18, %19};" ::"r"(ta),
+      "r"(ta + 8u), "r"(ta + (16u << 16)), "r"(ta + (16u << 16) + 8u), "r"(r[0]), "r"(r[1]),
+      "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // The same for one 16-lane half (lane offset already in ta): thread t holds
