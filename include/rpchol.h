@@ -126,7 +126,8 @@ typedef struct {
     double phase_ms[8];      /* profile mode: summed CUDA-event time per phase:
                                 0 propose, 1 H, 2 Algorithm 1, 3 operand prep,
                                 4 column step, 5 round control, 6 simple-RPC GEMV,
-                                7 simple-RPC finish */
+                                7 simple-RPC finish (scaling, d, tile sums, step
+                                end) */
     int64_t phase_launches[8];
     int64_t kernel_launches; /* kernels the last run launched on the device (the
                                 reset kernel plus every kernel of every loop body) */

@@ -142,6 +142,62 @@ __device__ __forceinline__ Real dist_term(int kind, Real t) {
   return kind == 4 ? (t < (Real)0 ? -t : t) : t * t;
 }
 
+// Accumulation type and 16-byte vector of a factor element type: FP32
+// factors (mixed mode) accumulate in FP32, FP64 factors in FP64.
+template <typename TF>
+struct FVec;
+template <>
+struct FVec<float> {
+  using V = float4;
+  using A = float;
+  static constexpr int E = 4;
+  __device__ static float dot(const float4 a, const float4 b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+  }
+};
+template <>
+struct FVec<double> {
+  using V = double2;
+  using A = double;
+  static constexpr int E = 2;
+  __device__ static double dot(const double2 a, const double2 b, double acc) {
+    acc = fma(a.x, b.x, acc);
+    return fma(a.y, b.y, acc);
+  }
+};
+
+// Dot products of R rows of a factor (16-byte aligned) with the vector v
+// over n elements, by one warp: lanes stride over 16-byte vectors (the R
+// rows' loads are independent), then the tail element by element, then a
+// butterfly reduction.  The results are valid in every lane.
+template <typename TF, int R>
+__device__ __forceinline__ void warp_rows_dot(const TF* const (&rows)[R], const TF* v,
+                                              long long n, int lane,
+                                              typename FVec<TF>::A (&acc)[R]) {
+  using V = typename FVec<TF>::V;
+  constexpr int E = FVec<TF>::E;
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0;
+  const long long nv = n / E;
+  const V* vv = (const V*)v;
+  for (long long m = lane; m < nv; m += 32) {
+    const V b = vv[m];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = FVec<TF>::dot(((const V*)rows[r])[m], b, acc[r]);
+  }
+  for (long long m = nv * E + lane; m < n; m += 32) {
+    const TF b = v[m];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] += rows[r][m] * b;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
 __host__ __device__ __forceinline__ long long round_up(long long a, long long b) {
   return (a + b - 1) / b * b;
 }

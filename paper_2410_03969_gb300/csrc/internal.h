@@ -61,7 +61,8 @@ struct DevBuffers {
   long long ldBs;
   double* Hpart;     // kHTilesMax x (kHSplitMax + 1) x 256: partial products of H, kernel entries
   int* hcnt;         // kHTilesMax arrival counters (zero between launches)
-  unsigned* ccnt;    // arrival counter of the tensor-core column step (zero between launches)
+  unsigned* ccnt;    // arrival counter of the tensor-core column step and of the simple
+                     // RPCholesky step (zero between launches)
   double* red;       // reduction scratch (trace error)
   long long nred;
   DevState* st;
@@ -126,9 +127,9 @@ cudaError_t launch_colstep_f64(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_colstep_f32_simt(const DevBuffers& b, int T, cudaStream_t s);
 
 // Simple RPCholesky (k_plain.cu)
-cudaError_t launch_plain_col(const DevBuffers& b, cudaStream_t s);
-cudaError_t launch_plain_finish(const DevBuffers& b, cudaStream_t s);
-cudaError_t launch_plain_end(const DevBuffers& b, unsigned long long cond, int use_cond,
-                             cudaStream_t s);
+// one step after the sampler: GEMV, new column and d; then tile sums and bookkeeping
+cudaError_t launch_plain_step(const DevBuffers& b, cudaStream_t s);
+cudaError_t launch_plain_tiles(const DevBuffers& b, unsigned long long cond, int use_cond,
+                               cudaStream_t s);
 
 }  // namespace rpchol

@@ -196,13 +196,13 @@ __device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float 
 // The kernel map of the epilogue in FP32 with the fast exponential
 // intrinsic: its error bound (2 + 1.16 |x|) ulp of exp(x) is an absolute
 // error below 1e-7 for every kernel value in (0, 1], the size of the FP32
-// rounding of the values it enters; r = r^2 rsqrt(r^2) adds at most a few
-// ulp to r.
+// rounding of the values it enters; r = r^2 rsqrt(max(r^2, 1e-30)) adds at
+// most a few ulp to r (and gives 0 at r = 0).
 template <int KIND>
 __device__ __forceinline__ float phi_fast(float inv_sigma, float r2) {
   r2 = r2 > 0.f ? r2 : 0.f;
   if (KIND == 0) return __expf(-0.5f * r2 * inv_sigma * inv_sigma);
-  const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+  const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
   if (KIND == 1) return __expf(-r * inv_sigma);
   if (KIND == 3) {
     const float t = 1.7320508075688772f * r * inv_sigma;
@@ -225,8 +225,10 @@ __device__ __forceinline__ void kappa_block(const EpiQuad& e, int j0, const floa
     const float ns = e.nrmSs[col];
 #pragma unroll
     for (int ri = 0; ri < 4; ++ri) {
-      const float kv =
-          col == e.jpiv[ri] ? 1.f : phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
+      // evaluated for every entry (no branch around the kernel map), then
+      // the row's own pivot column set to kappa(x, x) = 1
+      float kv = phi_fast<KIND>(e.inv_sigma, e.nr[ri] + ns - 2.f * D1v[ri][cj]);
+      kv = col == e.jpiv[ri] ? 1.f : kv;
       K[ri][cj] = col < e.s ? kv * kAccScale : 0.f;
     }
   }

@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(256) k_propose(DevState* st, const double* __r
                                                  const double* __restrict__ tile_sums,
                                                  double* tile_prefix, long long ntiles,
                                                  long long N, int* prop, double* uprop,
-                                                 double* uacc, int use_smem) {
+                                                 double* uacc, int use_smem, const void* F,
+                                                 long long ldF, int f_double) {
   extern __shared__ double pref_smem[];
   __shared__ double wsum[8];
   if (st->done) return;
@@ -197,6 +198,30 @@ __global__ void __launch_bounds__(256) k_propose(DevState* st, const double* __r
     uprop[j] = dvec[found];
     uacc[j] = ua;
   }
+  // simple RPCholesky (Algorithm 6): the pivot's entry of the new column,
+  // g_s = A(s,s) - ||F(s, 0:i)||^2 (A(s,s) = 1), with the arithmetic of the
+  // step's GEMV rows (FP32 accumulation for an FP32 factor)
+  if (st->plain && j == 0) {
+    const long long i = st->rank;
+    double g;
+    if (f_double) {
+      const double* fr = (const double*)F + found * ldF;
+      const double* rows[1] = {fr};
+      double acc[1];
+      warp_rows_dot<double, 1>(rows, fr, i, lane, acc);
+      g = 1.0 - acc[0];
+    } else {
+      const float* fr = (const float*)F + found * ldF;
+      const float* rows[1] = {fr};
+      float acc[1];
+      warp_rows_dot<float, 1>(rows, fr, i, lane, acc);
+      g = (double)(1.f - acc[0]);
+    }
+    if (lane == 0) {
+      st->gs = g;
+      st->piv = found;
+    }
+  }
 }
 
 cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s) {
@@ -214,7 +239,7 @@ cudaError_t launch_propose(const DevBuffers& b, int T, cudaStream_t s) {
   const int grid = (T + 7) / 8;
   k_propose<<<grid, 256, use_smem ? bytes : 0, s>>>(b.st, b.dvec, b.tile_sums, b.tile_prefix,
                                                     b.ntiles, b.N, b.prop, b.uprop, b.uacc,
-                                                    use_smem);
+                                                    use_smem, b.F, b.ldF, b.mixed ? 0 : 1);
   return cudaGetLastError();
 }
 

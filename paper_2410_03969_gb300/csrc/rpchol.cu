@@ -181,7 +181,7 @@ rpchol_status make_map(CUtensorMap* m, const void* base, unsigned long long inne
 
 // Phases of one loop-body iteration (profile-mode event slots):
 // 0 propose, 1 H, 2 Algorithm 1, 3 operand prep, 4 column step, 5 round end,
-// 6 simple-RPC GEMV, 7 simple-RPC finish.
+// 6 simple-RPC GEMV (new column and d), 7 simple-RPC finish (scaling, d, tile sums, step end).
 
 struct Phase {
   int slot;
@@ -212,21 +212,17 @@ cudaError_t ph_round_end(rpchol_ctx* c, int, unsigned long long cond, int use_co
   if (c->use_tc) return cudaSuccess;  // the tensor-core column step closed the round
   return launch_round_end(c->b, cond, use_cond, s);
 }
-cudaError_t ph_plain_col(rpchol_ctx* c, int, unsigned long long, int, cudaStream_t s) {
-  return launch_plain_col(c->b, s);
+cudaError_t ph_plain_step(rpchol_ctx* c, int, unsigned long long, int, cudaStream_t s) {
+  return launch_plain_step(c->b, s);
 }
-cudaError_t ph_plain_finish(rpchol_ctx* c, int, unsigned long long, int, cudaStream_t s) {
-  return launch_plain_finish(c->b, s);
-}
-cudaError_t ph_plain_end(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
-                         cudaStream_t s) {
-  return launch_plain_end(c->b, cond, use_cond, s);
+cudaError_t ph_plain_tiles(rpchol_ctx* c, int, unsigned long long cond, int use_cond,
+                           cudaStream_t s) {
+  return launch_plain_tiles(c->b, cond, use_cond, s);
 }
 
 const Phase kAccelPhases[] = {{0, ph_propose}, {1, ph_hmat},    {2, ph_reject},
                               {3, ph_prep},    {4, ph_colstep}, {5, ph_round_end}};
-const Phase kPlainPhases[] = {
-    {0, ph_propose}, {6, ph_plain_col}, {7, ph_plain_finish}, {5, ph_plain_end}};
+const Phase kPlainPhases[] = {{0, ph_propose}, {6, ph_plain_step}, {7, ph_plain_tiles}};
 
 // One iteration of the loop body: one round of Algorithm 2, or one step of
 // Algorithm 6.  With `ev` (profile mode) every phase is bracketed by a pair
@@ -234,7 +230,7 @@ const Phase kPlainPhases[] = {
 cudaError_t launch_body(rpchol_ctx* c, int plain, int T, unsigned long long cond, int use_cond,
                         cudaStream_t s, std::vector<ProfRec>* ev = nullptr, long long iter = 0) {
   const Phase* ph = plain ? kPlainPhases : kAccelPhases;
-  const int n = plain ? 4 : 6;
+  const int n = plain ? 3 : 6;
   for (int i = 0; i < n; ++i) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (ev) {
@@ -724,9 +720,10 @@ rpchol_status rpchol_stats(rpchol_ctx* c, rpchol_run_stats* out) {
     // prep (prep and W blocks in one launch for the tensor-core step, the
     // gather otherwise), column step, round end (closed by the tensor-core
     // column step itself);
-    // simple = propose, GEMV, finish, step end.  The graph runs the body once
+    // simple = propose (with g_s), GEMV and new column, tile sums and step end.
+    // The graph runs the body once
     // per round; the host loop launches whole chunks of bodies.
-    const long long per = c->last_plain ? 4 : (c->use_tc ? 5 : 6);
+    const long long per = c->last_plain ? 3 : (c->use_tc ? 5 : 6);
     const long long iters = c->host_iters >= 0 ? c->host_iters : st.round;
     out->kernel_launches = c->has_run ? 1 + per * iters : 0;
   }
