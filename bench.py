@@ -214,12 +214,20 @@ def batched_measure(args):
     log("  one by one done")
     seq_ms = min(timed(lambda: one_by_one(100 + 1000 * r)) for r in range(2))
     with rp.Batch(fs, Ts) as b:
-        log("  batch recorded")
+        mode = b.mode
+        log("  batch set up (%s)" % ("engine" if mode == rp.BATCH_ENGINE else "graph"))
         b.run(ks, [7 + i for i in range(len(fs))])
         bms = [timed(lambda: b.run(ks, [200 + 1000 * r + i for i in range(len(fs))]))
                for r in range(10)]
         bat_ms = statistics.median(bms)
         terr = [f.stats()["trace_error"] for f in fs[:16]]
+        graph_ms = None
+        if mode == rp.BATCH_ENGINE:
+            b.mode = rp.BATCH_GRAPH  # the graph executor on the same instances, for context
+            b.run(ks, [7 + i for i in range(len(fs))])
+            graph_ms = statistics.median(
+                timed(lambda: b.run(ks, [300 + 1000 * r + i for i in range(len(fs))]))
+                for r in range(3))
     for f in fs:
         f.close()
     piv = sum(ks)
@@ -232,7 +240,10 @@ def batched_measure(args):
             "speedup_vs_one_by_one": seq_ms / bat_ms, "autotune_s": tune_s,
             "shape_classes": len(classes), "T_chosen": sorted(set(Ts)),
             "trace_error_mean_first16": statistics.mean(terr),
-            "launch": "one CUDA graph, one conditional round loop per instance"}
+            "graph_executor_ms": graph_ms,
+            "launch": ("one persistent launch: clusters of 8 CTAs take instances from a device "
+                       "queue, largest N k^2 first" if mode == rp.BATCH_ENGINE else
+                       "one CUDA graph, one conditional round loop per instance")}
 
 
 def serving_measure(args):

@@ -351,23 +351,49 @@ rpchol_status rpchol_rpqr_destroy(rpchol_rpqr* ctx);
 
 /* ---------------------------------------------------------------- batches
  * Many independent factorisations (Algorithm 2 each, arXiv 2410.03969 §3)
- * in one launch: the batch records one CUDA graph in which every context
- * has its own branch, a reset kernel followed by a conditional while-loop
- * over that context's rounds (the loop body is the same kernel sequence
- * rpchol_run launches).  Branches are independent, so the GPU overlaps the
- * instances' small kernels (sampler, H, Algorithm 1) with the others'
- * column steps.  Each context keeps its own buffers and results; after a
- * batch run, rpchol_stats / rpchol_factor / rpchol_copy_factor* on a
- * context see that context's run (its stream waits for the batch).
+ * in one launch.  Two executors:
+ *
+ *   RPCHOL_BATCH_ENGINE: one persistent kernel launch.  Its grid is made of
+ *     clusters of 8 CTAs (one CTA per SM, as many clusters as can be
+ *     resident).  Instances are admitted from a device queue in the order
+ *     of their expected work N k^2, largest first.  Each round of an
+ *     instance is one control job (sampler, H, Algorithm 1, operand prep)
+ *     that a whole cluster runs, then a column step split into tile parts
+ *     that any CTA of any cluster takes; the CTA finishing the last part
+ *     closes the round and frees the next control job.  Needs every context
+ *     in mixed precision with the tensor-core column step (N >= 128, not
+ *     the l1-Laplace kernel) and T_max <= 256.
+ *   RPCHOL_BATCH_GRAPH: one CUDA graph in which every context has its own
+ *     branch, a reset kernel followed by a conditional while-loop over that
+ *     context's rounds (the loop body is the kernel sequence rpchol_run
+ *     launches).  Any precision.
+ *
+ * Both run each phase with the block decomposition rpchol_run uses, so an
+ * instance's pivots and factor are bit-identical to rpchol_run's.  Each
+ * context keeps its own buffers and results; after a batch run,
+ * rpchol_stats / rpchol_factor / rpchol_copy_factor* on a context see that
+ * context's run (its stream waits for the batch).
  * The paper runs one factorisation at a time; it has no batched form.     */
 typedef struct rpchol_batch rpchol_batch;
 
-/* Record the batch graph for n >= 1 contexts (all on the current device)
- * with block sizes T[i] (1 <= T[i] <= that context's T_max).  The batch
- * borrows the contexts: destroy it before any of them.  Errors: EINVAL
- * (n < 1, NULL context, T out of range, a context twice), ENOMEM, ECUDA.  */
+#define RPCHOL_BATCH_GRAPH 0
+#define RPCHOL_BATCH_ENGINE 1
+
+/* Set up a batch of n >= 1 contexts (all on the current device) with block
+ * sizes T[i] (1 <= T[i] <= that context's T_max): the engine when every
+ * context supports it, else the graph.  The batch borrows the contexts:
+ * destroy it before any of them.  Errors: EINVAL (n < 1, NULL context, T
+ * out of range, a context twice), ENOMEM, ECUDA.                          */
 rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int32_t* T,
                                   rpchol_batch** out);
+
+/* Switch the executor for later runs (RPCHOL_BATCH_GRAPH records the graph
+ * on first use).  Errors: EINVAL (unknown mode, or the engine when a member
+ * does not support it), ENOMEM, ECUDA.                                     */
+rpchol_status rpchol_batch_set_mode(rpchol_batch* batch, int32_t mode);
+
+/* The executor in use; -1 for NULL.                                        */
+int32_t rpchol_batch_mode(const rpchol_batch* batch);
 
 /* Run every instance once: instance i to rank k[i] (1 <= k[i] <= its
  * k_max) with Philox seed seeds[i] (the same stream contract as

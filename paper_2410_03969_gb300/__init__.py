@@ -115,6 +115,8 @@ _SIGNATURES = [
     ("rpchol_batch_run", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]),
     ("rpchol_batch_destroy", None, [ctypes.c_void_p]),
+    ("rpchol_batch_set_mode", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("rpchol_batch_mode", ctypes.c_int32, [ctypes.c_void_p]),
     ("rpchol_context_bytes", ctypes.c_int64, [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                               ctypes.c_int32, ctypes.c_int32]),
     ("rpchol_server_create", ctypes.c_int, [ctypes.c_int64, ctypes.c_int32,
@@ -459,10 +461,17 @@ class RPQR:
         self.close()
 
 
+BATCH_GRAPH = 0
+BATCH_ENGINE = 1
+
+
 class Batch:
-    """Several Factorizers run together in one launch (one CUDA graph with a
-    conditional round loop per instance); instance i uses block size T[i].
-    Destroy (close) the batch before its factorizers."""
+    """Several Factorizers run together in one launch; instance i uses block
+    size T[i].  `mode` is the executor: BATCH_ENGINE (one persistent launch of
+    clusters taking instances from a device queue; mixed precision with the
+    tensor-core column step) or BATCH_GRAPH (one CUDA graph with a conditional
+    round loop per instance).  Destroy (close) the batch before its
+    factorizers."""
 
     def __init__(self, factorizers, T):
         self.members = list(factorizers)
@@ -473,6 +482,14 @@ class Batch:
         _check(lib().rpchol_batch_create(ctxs, n, Ts, ctypes.byref(self._b)),
                "rpchol_batch_create")
         self.T = [int(t) for t in T]
+
+    @property
+    def mode(self):
+        return int(lib().rpchol_batch_mode(self._b))
+
+    @mode.setter
+    def mode(self, m):
+        _check(lib().rpchol_batch_set_mode(self._b, int(m)), "rpchol_batch_set_mode")
 
     def run(self, k, seeds, stream=None):
         n = len(self.members)

@@ -202,6 +202,13 @@ __host__ __device__ __forceinline__ long long round_up(long long a, long long b)
   return (a + b - 1) / b * b;
 }
 
+// The round bodies written for 256 threads (sampler, H, W blocks) use this
+// barrier instead of __syncthreads: in their own 256-thread kernels it spans
+// the CTA; inside a larger persistent CTA only its first 256 threads run
+// them and take part.
+constexpr int kBodyThreads = 256;
+__device__ __forceinline__ void body_sync() { asm volatile("bar.sync 8, 256;" ::: "memory"); }
+
 // Fixed-order block reduction of one double per thread (blockDim.x threads,
 // a multiple of 32).  Result valid in thread 0.
 __device__ __forceinline__ double block_sum_fixed(double v, double* red_smem) {

@@ -126,6 +126,19 @@ cudaError_t launch_widen_f32(const float* F, long long ldF, long long N, long lo
 cudaError_t launch_colstep_f64(const DevBuffers& b, int T, cudaStream_t s);
 cudaError_t launch_colstep_f32_simt(const DevBuffers& b, int T, cudaStream_t s);
 
+// Persistent batch engine (k_batch.cu): whether a context can run in it
+// (mixed mode with the tensor-core column step), the number of CTAs of a
+// launch (whole clusters that fit at once), the device records of a batch's
+// contexts, the bytes of the scheduler state (zeroed before every launch),
+// and one launch over n instances admitted in the order `order`.
+bool engine_supported(const DevBuffers& b, int use_tc);
+cudaError_t engine_grid(int* ctas);
+cudaError_t engine_setup(int n, const DevBuffers* bs, const TcMaps* ms, void** insts_dev,
+                         void** maps_dev, cudaStream_t s);
+size_t engine_queue_bytes(int n);
+cudaError_t engine_launch(const void* insts_dev, const void* maps_dev, const RunParams* params,
+                          const int* order, int n, void* queue, int ctas, cudaStream_t s);
+
 // Simple RPCholesky (k_plain.cu)
 // one step after the sampler: GEMV, new column and d; then tile sums and bookkeeping
 cudaError_t launch_plain_step(const DevBuffers& b, cudaStream_t s);

@@ -18,143 +18,19 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "prep_body.cuh"
 #include "tc_ptx.cuh"
 
 namespace rpchol {
 
-// Byte offset of the 16-byte piece q (0..3) of row j in a 64-byte-row image
-// with the 64-byte swizzle (piece q of row j sits at q ^ ((j >> 1) & 3)).
-__device__ __forceinline__ int sw64_off(int j, int q) { return j * 64 + 16 * (q ^ ((j >> 1) & 3)); }
-
-// Row j of the B images (one CTA per row).
-__device__ __forceinline__ void prep_row(const DevState* st, const float* __restrict__ F,
-                                         long long ldF, const float* __restrict__ X, int xld,
-                                         const float* __restrict__ nrm,
-                                         const int* __restrict__ Sacc, unsigned char* Bf,
-                                         unsigned char* Bx, float* nrmS, int j) {
-  const int s = st->s;
-  if (s == 0) return;
-  const long long rank = st->rank;
-  const int s_pad = (s + 15) & ~15;
-  if (j >= s_pad) return;
-  const size_t cb = 128 * (size_t)s_pad;  // bytes of one chunk image
-  const int nF = (int)((rank + 31) >> 5);
-  const int nXc = xld >> 4;
-  const int p = j < s ? Sacc[j] : -1;
-  const float* frow = p >= 0 ? F + (long long)p * ldF : nullptr;
-  const float* xrow = p >= 0 ? X + (long long)p * xld : nullptr;
-  for (int it = threadIdx.x; it < 4 * nF; it += blockDim.x) {
-    const int c = it >> 2, q = it & 3;
-    const long long col = 32ll * c + 8 * q;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = (frow && col + e < rank) ? -4096.f * frow[col + e] : 0.f;
-    uint32_t hw[4], lw[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const __half2 h = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
-      const float2 hf = __half22float2(h);
-      const __half2 l = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-      hw[e] = *(const uint32_t*)&h;
-      lw[e] = *(const uint32_t*)&l;
-    }
-    unsigned char* base = Bf + (size_t)c * cb + sw64_off(j, q);
-    *(uint4*)base = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *(uint4*)(base + 64 * s_pad) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  }
-  for (int it = threadIdx.x; it < 4 * nXc; it += blockDim.x) {
-    const int c = it >> 2, q = it & 3;
-    const int col = 16 * c + 4 * q;
-    float h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float v = xrow ? xrow[col + e] : 0.f;
-      h[e] = tc::tf32_head(v);
-      l[e] = v - h[e];
-    }
-    unsigned char* base = Bx + (size_t)c * cb + sw64_off(j, q);
-    *(float4*)base = make_float4(h[0], h[1], h[2], h[3]);
-    *(float4*)(base + 64 * s_pad) = make_float4(l[0], l[1], l[2], l[3]);
-  }
-  if (threadIdx.x == 0) nrmS[j] = p >= 0 ? nrm[p] : 0.f;
-}
-
-// Blocked forward substitution operand for G L^* = R.  With the columns in
-// blocks of 16 (block b covers columns j0 = 16 b .. j0 + 15) and D_b the
-// 16 x 16 diagonal block of L, block b of G is
-//   G_b = D_b^{-1} (R_b - G_{<j0} L(b, <j0)^*)
-//       = sum_{l < j0} G(:, l) W_b(l, :) + sum_{m < 16} R(:, j0 + m) W_b(j0 + m, :)
-// with W_b(l, jj) = -(D_b^{-1} L(b, <j0))(jj, l) for l < j0 and
-// W_b(j0 + m, jj) = D_b^{-1}(jj, m).  All of it is formed here in FP64 from
-// the FP64 L of Algorithm 1 and rounded once to FP32.  Block b occupies
-// (j0 + 16) x 16 floats at offset 256 b (b + 1) / 2, row l contiguous.
-// Rows and columns of L beyond s are taken as the identity, so padded
-// columns of G are copies of the (zero) padded columns of R.
-// One CTA per block b and part of the range l < j0 (part 0 also writes the
-// diagonal rows).  Each CTA forms D_b^{-1} itself, by rows (row c is final
-// once rows < c are), one step per row for the whole CTA.
-__device__ __forceinline__ void wblk(const DevState* st, const double* __restrict__ L, int ldL,
-                                     float* W, int b, int part, int nparts) {
-  __shared__ double Db[16][17];
-  __shared__ double acc[16][17];
-  __shared__ double Dinv[16][17];
-  __shared__ double rdiag[16];
-  __shared__ double Lb[16][33];  // rows j0..j0+15 of L, columns l0..l1-1
-  const int s = st->s;
-  const int j0 = 16 * b;
-  if (j0 >= s) return;
-  const int per = (j0 + nparts - 1) / nparts;  // <= 32
-  const int l0 = part * per;
-  const int l1 = l0 + per < j0 ? l0 + per : j0;
-  if (part > 0 && l0 >= l1) return;
-  const int nl = l1 > l0 ? l1 - l0 : 0;
-  const int t = threadIdx.x, r = t >> 4, m = t & 15;
-  auto Lat = [&](int rr, int cc) -> double {  // L with identity padding beyond s
-    if (rr >= s || cc >= s) return rr == cc ? 1.0 : 0.0;
-    return cc <= rr ? L[(long long)rr * ldL + cc] : 0.0;
-  };
-  Db[r][m] = Lat(j0 + r, j0 + m);
-  acc[r][m] = r == m ? 1.0 : 0.0;
-  if (t < 16) rdiag[t] = 1.0 / Lat(j0 + t, j0 + t);
-  for (int e = t; e < 16 * nl; e += 256) Lb[e / nl][e % nl] = Lat(j0 + e / nl, l0 + e % nl);
-  __syncthreads();
-  // D_b^{-1}(c, :) = (e_c - sum_{c' < c} D_b(c, c') D_b^{-1}(c', :)) / D_b(c, c)
-  for (int c = 0; c < 16; ++c) {
-    if (r >= c) {
-      const double xc = acc[c][m] * rdiag[c];
-      if (r == c) Dinv[c][m] = xc;
-      else acc[r][m] = fma(-Db[r][c], xc, acc[r][m]);
-    }
-    __syncthreads();
-  }
-  float* Wb = W + 256 * (long long)b * (b + 1) / 2;
-  for (int e = t; e < 16 * nl; e += 256) {  // W_b(l, jj), l0 <= l < l1
-    const int l = e >> 4, jj = e & 15;
-    double a = 0.0;
-    for (int mm = 0; mm <= jj; ++mm) a = fma(Dinv[jj][mm], Lb[mm][l], a);
-    Wb[(long long)(l0 + l) * 16 + jj] = (float)(-a);
-  }
-  if (part == 0)  // W_b(j0 + m, jj) = D_b^{-1}(jj, m)
-    Wb[(long long)(j0 + r) * 16 + m] = (float)Dinv[m][r];
-}
-
-// One launch for both: CTAs [0, kTMax) prepare the rows of the B operands,
-// CTAs [kTMax, kTMax + 8 kTMax / 16) form the W blocks (block b, part p at
-// kTMax + 8 b + p).  The two have no data in common and run side by side.
-constexpr int kWParts = 8;
 __global__ void __launch_bounds__(256) k_prep_tc(const DevState* st, const float* __restrict__ F,
                                                  long long ldF, const float* __restrict__ X,
                                                  int xld, const float* __restrict__ nrm,
                                                  const int* __restrict__ Sacc, unsigned char* Bf,
                                                  unsigned char* Bx, float* nrmS,
                                                  const double* __restrict__ L, int ldL, float* W) {
-  if (st->done) return;
-  if (blockIdx.x < kTMax) {
-    prep_row(st, F, ldF, X, xld, nrm, Sacc, Bf, Bx, nrmS, (int)blockIdx.x);
-  } else {
-    const int i = (int)blockIdx.x - kTMax;
-    wblk(st, L, ldL, W, i / kWParts, i % kWParts, kWParts);
-  }
+  __shared__ WblkSmem S;
+  prep_block((int)blockIdx.x, S, st, F, ldF, X, xld, nrm, Sacc, Bf, Bx, nrmS, L, ldL, W);
 }
 
 __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, float* Xl) {
@@ -167,7 +43,7 @@ __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, f
 }
 
 cudaError_t launch_prep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {
-  k_prep_tc<<<kTMax + kWParts * (kTMax / 16), 256, 0, s>>>(
+  k_prep_tc<<<kPrepBlocks, 256, 0, s>>>(
       b.st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc, m.Bf, m.Bx, m.nrmS, b.L, b.Tmax,
       m.Linv32);
   return cudaGetLastError();

@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <vector>
@@ -931,6 +932,15 @@ struct rpchol_batch {
   cudaEvent_t done = nullptr;      // last batch run done
   cudaStream_t cap = nullptr;      // private stream used only to record
   bool ran = false;
+  // persistent engine (mode RPCHOL_BATCH_ENGINE)
+  int mode = RPCHOL_BATCH_GRAPH;
+  bool engine_ok = false;          // every member supports the engine
+  void* insts = nullptr;           // device: instance descriptors
+  void* maps = nullptr;            // device: tensor maps
+  int* dorder = nullptr;           // device: queue order
+  void* dqueue = nullptr;          // device: scheduler state (zeroed every run)
+  int* horder = nullptr;           // pinned staging of the order
+  int ctas = 0;                    // engine grid (whole clusters, all resident)
 };
 
 namespace {
@@ -943,10 +953,33 @@ void batch_release(rpchol_batch* b) {
   if (b->done) cudaEventSynchronize(b->done), cudaEventDestroy(b->done);
   if (b->dparams) cudaFree(b->dparams);
   if (b->hparams) cudaFreeHost(b->hparams);
+  if (b->insts) cudaFree(b->insts);
+  if (b->maps) cudaFree(b->maps);
+  if (b->dorder) cudaFree(b->dorder);
+  if (b->dqueue) cudaFree(b->dqueue);
+  if (b->horder) cudaFreeHost(b->horder);
   if (b->cap) cudaStreamDestroy(b->cap);
 }
 
+// Descriptors, queue and grid of the persistent engine.
+rpchol_status engine_prepare(rpchol_batch* b) {
+  const int n = (int)b->ctxs.size();
+  std::vector<DevBuffers> bs(n);
+  std::vector<TcMaps> ms(n);
+  for (int i = 0; i < n; ++i) {
+    bs[i] = b->ctxs[i]->b;
+    ms[i] = b->ctxs[i]->tc;
+  }
+  CU(engine_grid(&b->ctas));
+  CU(cudaMalloc((void**)&b->dorder, sizeof(int) * (size_t)n));
+  CU(cudaMalloc(&b->dqueue, engine_queue_bytes(n)));
+  CU(cudaMallocHost((void**)&b->horder, sizeof(int) * (size_t)n));
+  CU(engine_setup(n, bs.data(), ms.data(), &b->insts, &b->maps, b->cap));
+  return RPCHOL_OK;
+}
+
 rpchol_status batch_record(rpchol_batch* b) {
+  if (b->exec) return RPCHOL_OK;
   const int n = (int)b->ctxs.size();
   CU(cudaGraphCreate(&b->graph, 0));
   for (int i = 0; i < n; ++i) {
@@ -1045,11 +1078,49 @@ rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int3
     if (e == cudaSuccess) b->ready.push_back(ev);
   }
   if (e != cudaSuccess) return fail(cuda_fail(e, "batch setup"));
-  rpchol_status rs = batch_record(b);
+  b->engine_ok = true;
+  for (int i = 0; i < n; ++i) {
+    const rpchol_ctx* c = ctxs[i];
+    b->engine_ok = b->engine_ok && c->precision == RPCHOL_MIXED && c->use_tc &&
+                   engine_supported(c->b, c->use_tc);
+  }
+  rpchol_status rs;
+  if (b->engine_ok) {
+    rs = engine_prepare(b);
+    b->mode = RPCHOL_BATCH_ENGINE;
+  } else {
+    rs = batch_record(b);
+    b->mode = RPCHOL_BATCH_GRAPH;
+  }
   if (rs != RPCHOL_OK) return fail(rs);
   *out = b;
   return RPCHOL_OK;
 }
+
+rpchol_status rpchol_batch_set_mode(rpchol_batch* b, int32_t mode) {
+  g_err[0] = 0;
+  if (!b || (mode != RPCHOL_BATCH_GRAPH && mode != RPCHOL_BATCH_ENGINE)) {
+    set_err("invalid argument: mode=%d", mode);
+    return RPCHOL_EINVAL;
+  }
+  if (mode == RPCHOL_BATCH_ENGINE && !b->engine_ok) {
+    set_err("the batch engine needs every member in mixed precision with the tensor-core "
+            "column step (N >= 128) and T_max <= %d",
+            kTMax);
+    return RPCHOL_EINVAL;
+  }
+  if (mode == RPCHOL_BATCH_GRAPH) {
+    rpchol_status rs = batch_record(b);
+    if (rs != RPCHOL_OK) return rs;
+  } else if (!b->insts) {
+    rpchol_status rs = engine_prepare(b);
+    if (rs != RPCHOL_OK) return rs;
+  }
+  b->mode = mode;
+  return RPCHOL_OK;
+}
+
+int32_t rpchol_batch_mode(const rpchol_batch* b) { return b ? b->mode : -1; }
 
 rpchol_status rpchol_batch_run(rpchol_batch* b, const int64_t* k, const uint64_t* seeds,
                                void* stream) {
@@ -1083,8 +1154,22 @@ rpchol_status rpchol_batch_run(rpchol_batch* b, const int64_t* k, const uint64_t
   }
   CU(cudaMemcpyAsync(b->dparams, b->hparams, sizeof(RunParams) * (size_t)n,
                      cudaMemcpyHostToDevice, s));
-  CU(cudaEventRecord(b->copied, s));
-  CU(cudaGraphLaunch(b->exec, s));
+  if (b->mode == RPCHOL_BATCH_ENGINE) {
+    // queue order: largest expected work (N k^2) first, ties in index order
+    std::vector<double> w(n);
+    for (int i = 0; i < n; ++i)
+      w[i] = (double)b->ctxs[i]->b.N * (double)k[i] * (double)k[i];
+    for (int i = 0; i < n; ++i) b->horder[i] = i;
+    std::stable_sort(b->horder, b->horder + n, [&](int x, int y) { return w[x] > w[y]; });
+    CU(cudaMemcpyAsync(b->dorder, b->horder, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
+                       s));
+    CU(cudaMemsetAsync(b->dqueue, 0, engine_queue_bytes(n), s));
+    CU(cudaEventRecord(b->copied, s));
+    CU(engine_launch(b->insts, b->maps, b->dparams, b->dorder, n, b->dqueue, b->ctas, s));
+  } else {
+    CU(cudaEventRecord(b->copied, s));
+    CU(cudaGraphLaunch(b->exec, s));
+  }
   CU(cudaEventRecord(b->done, s));
   for (int i = 0; i < n; ++i) {
     rpchol_ctx* c = b->ctxs[i];
