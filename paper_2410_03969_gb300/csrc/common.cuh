@@ -17,6 +17,12 @@ constexpr int kTMax = 256;
 // most ways the rank dimension of H = A(S',S') - F(S',:)F(S',:)^* is split
 constexpr int kHSplitMax = 8;
 constexpr int kHTilesMax = (kTMax / 16) * (kTMax / 16 + 1) / 2;
+constexpr int kH32BlocksMax = (kTMax / 32) * (kTMax / 32 + 1) / 2;
+// partial products of H: 16 x 16 tiles (FP64 factor) or 32 x 32 blocks (FP32 factor)
+constexpr long long kHPartDoubles =
+    (long long)kHTilesMax * (kHSplitMax + 1) * 256 > (long long)kH32BlocksMax * (kHSplitMax + 1) * 1024
+        ? (long long)kHTilesMax * (kHSplitMax + 1) * 256
+        : (long long)kH32BlocksMax * (kHSplitMax + 1) * 1024;
 // Leading dimensions are padded to this many elements.
 constexpr int kLdAlign = 32;
 

@@ -59,7 +59,7 @@ struct DevBuffers {
   long long ldB;
   float* Bs32;       // mixed mode: T_max x ldBs rows of the column-step operand
   long long ldBs;
-  double* Hpart;     // kHTilesMax x (kHSplitMax + 1) x 256: partial products of H, kernel entries
+  double* Hpart;     // kHPartDoubles: partial products of H, kernel entries
   int* hcnt;         // kHTilesMax arrival counters (zero between launches)
   unsigned* ccnt;    // arrival counter of the tensor-core column step and of the simple
                      // RPCholesky step (zero between launches)

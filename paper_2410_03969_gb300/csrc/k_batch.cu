@@ -193,24 +193,23 @@ __device__ __noinline__ void decide(EngineQueue* q, EngineSlot* slots, const Eng
     if (ld_acquire_s32(&q->abort)) whole.kind = kJobExit;
     int A = ld_acquire_s32(&q->admitted);
     if (A > n) A = n;
-    // step over the finished prefix of the queue
-    while (whole.kind == kJobNone && lo < A) {
-      const int a = lo + lane;
-      const bool stop = a >= A || !ld_acquire_s32(&slots[a].finished);
-      const unsigned m = __ballot_sync(0xffffffffu, stop);
-      if (m == 0u) {
-        lo += 32;
-        continue;
-      }
-      lo += __ffs(m) - 1;
-      break;
-    }
-    // a control job (the whole cluster), earliest admitted first
-    for (int base = lo; whole.kind == kJobNone && base < A; base += 32) {
+    // one pass over the admitted positions from lo: the finished prefix is
+    // stepped over; a control job (the whole cluster) is taken first,
+    // earliest admitted first; else tile parts of open column steps, one per
+    // CTA, claimed several at a time with one atomic per instance
+    for (int base = lo; whole.kind == kJobNone && assigned < kEngCluster && base < A;
+         base += 32) {
       const int a = base + lane;
-      const bool c = a < A && *(volatile const int*)&slots[a].ctrl == 1;
-      unsigned m = __ballot_sync(0xffffffffu, c);
-      while (m) {
+      const bool in = a < A;
+      const int fin = in ? *(volatile const int*)&slots[a].finished : 1;
+      const int ctl = in ? *(volatile const int*)&slots[a].ctrl : 0;
+      const unsigned long long tk = in ? ld_relaxed_u64(&slots[a].tickets) : 0ull;
+      if (base == lo) {
+        const unsigned mu = __ballot_sync(0xffffffffu, !fin || !in);
+        if (mu != 1u) lo += (mu == 0u ? 32 : __ffs(mu) - 1);  // finished prefix
+      }
+      unsigned m = __ballot_sync(0xffffffffu, !fin && ctl == 1);
+      while (m && assigned == 0) {
         const int src = __ffs(m) - 1;
         m &= m - 1;
         int got = 0;
@@ -221,25 +220,18 @@ __device__ __noinline__ void decide(EngineQueue* q, EngineSlot* slots, const Eng
           break;
         }
       }
-    }
-    // else tile parts of open column steps, one per CTA
-    for (int base = lo; whole.kind == kJobNone && assigned < kEngCluster && base < A;
-         base += 32) {
-      const int a = base + lane;
-      const unsigned long long tk = a < A ? ld_relaxed_u64(&slots[a].tickets) : 0ull;
-      const bool open = (unsigned)(tk & 0xffffffffull) < (unsigned)(tk >> 32);
-      unsigned m = __ballot_sync(0xffffffffu, open);
+      if (whole.kind != kJobNone) break;
+      const bool open = !fin && (unsigned)(tk & 0xffffffffull) < (unsigned)(tk >> 32);
+      m = __ballot_sync(0xffffffffu, open);
       while (m && assigned < kEngCluster) {
         const int src = __ffs(m) - 1;
         m &= m - 1;
         if (lane == src) {
-          while (assigned < kEngCluster) {
-            const unsigned long long old = atom_add_acq_rel(&slots[a].tickets, 1ull);
-            const unsigned p = (unsigned)(old & 0xffffffffull), parts = (unsigned)(old >> 32);
-            if (p >= parts) break;
-            tl.plan[assigned] = Job{kJobTile, a, (int)p, (int)parts};
-            ++assigned;
-          }
+          const unsigned want = (unsigned)(kEngCluster - assigned);
+          const unsigned long long old = atom_add_acq_rel(&slots[a].tickets, want);
+          const unsigned p = (unsigned)(old & 0xffffffffull), parts = (unsigned)(old >> 32);
+          for (unsigned i = 0; i < want && p + i < parts; ++i)
+            tl.plan[assigned++] = Job{kJobTile, a, (int)(p + i), (int)parts};
         }
         assigned = __shfl_sync(0xffffffffu, assigned, src);
       }
@@ -310,14 +302,11 @@ __device__ __forceinline__ void control_job(const Job& J, const EngineInst* inst
   phase_sync();
   // ---- step 2: H = A(S',S') - F(S',:) F(S',:)^* (256-thread body)
   if (tid < kBodyThreads) {
-    const int nbh = (T + 15) / 16, ntile = nbh * (nbh + 1) / 2;
-    const int ks = hmat_splits(ntile, b.num_sms);
-    float(*Fa)[33] = (float(*)[33])sm;
-    float(*Fb)[33] = (float(*)[33])(sm + 16 * 33 * sizeof(float));
-    int& last = *(int*)(sm + 2 * 16 * 33 * sizeof(float));
-    for (int it = (int)cr; it < ntile * ks; it += kEngCluster) {
-      hmat_body<float>(it / ks, it % ks, ks, Fa, Fb, last, st, b.X, b.xld, b.d, b.kind,
-                       1.0 / b.sigma, (const float*)b.F, b.ldF, b.prop, b.H, b.Hpart, b.hcnt);
+    const int nblk = hmat32_blocks(T), ks = hmat32_splits(nblk);
+    H32Smem& S = *(H32Smem*)sm;
+    for (int it = (int)cr; it < nblk * ks; it += kEngCluster) {
+      hmat32_body(it / ks, it % ks, ks, S, st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
+                  (const float*)b.F, b.ldF, b.prop, b.H, b.Hpart, b.hcnt);
       body_sync();
     }
   }
@@ -338,20 +327,17 @@ __device__ __forceinline__ void control_job(const Job& J, const EngineInst* inst
     }
     return;
   }
-  // ---- operand images (every thread) and W blocks (256-thread body)
-  {
+  // ---- operand images (every thread, rows cr, cr + 8, ...) and W blocks
+  // (256-thread body, blocks cr, cr + 8, ...): the bytes the stand-alone
+  // prep writes
+  prep_rows_strided(st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc,
+                    (unsigned char*)I.ta.Bf, (unsigned char*)I.ta.Bx, (float*)I.ta.nrmS, (int)cr,
+                    kEngCluster);
+  if (tid < kBodyThreads) {
     WblkSmem& S = *(WblkSmem*)sm;
-    for (int blk = (int)cr; blk < kPrepBlocks; blk += kEngCluster) {
-      if (blk < kTMax) {
-        prep_block(blk, S, st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc,
-                   (unsigned char*)I.ta.Bf, (unsigned char*)I.ta.Bx, (float*)I.ta.nrmS, b.L,
-                   b.Tmax, (float*)I.ta.W);
-      } else if (tid < kBodyThreads) {
-        prep_block(blk, S, st, (const float*)b.F, b.ldF, b.X, b.xld, b.nrm, b.Sacc,
-                   (unsigned char*)I.ta.Bf, (unsigned char*)I.ta.Bx, (float*)I.ta.nrmS, b.L,
-                   b.Tmax, (float*)I.ta.W);
-        body_sync();
-      }
+    for (int wb = (int)cr; wb < kTMax / 16; wb += kEngCluster) {
+      wblk_full(S, st, b.L, b.Tmax, (float*)I.ta.W, wb);
+      body_sync();
     }
   }
   phase_sync();

@@ -103,17 +103,30 @@ __global__ void __launch_bounds__(256) k_hmat(const DevState* st, const float* _
                 F, ldF, prop, H, Hpart, hcnt);
 }
 
+__global__ void __launch_bounds__(256) k_hmat32(const DevState* st, const float* __restrict__ X,
+                                                int xld, int d, int kind, double inv_sigma,
+                                                const float* __restrict__ F, long long ldF,
+                                                const int* __restrict__ prop, double* H,
+                                                double* Hpart, int* hcnt) {
+  __shared__ H32Smem S;
+  hmat32_body(blockIdx.x, blockIdx.y, gridDim.y, S, st, X, xld, d, kind, inv_sigma, F, ldF, prop,
+              H, Hpart, hcnt);
+}
+
 cudaError_t launch_hmat(const DevBuffers& b, int T, cudaStream_t s) {
-  const int nb = (T + 15) / 16;
-  const int ntile = nb * (nb + 1) / 2;
-  const int ks = hmat_splits(ntile, b.num_sms);
-  dim3 grid(ntile, ks);
-  if (b.mixed)
-    k_hmat<float><<<grid, 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
-                                       (const float*)b.F, b.ldF, b.prop, b.H, b.Hpart, b.hcnt);
-  else
-    k_hmat<double><<<grid, 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
-                                        (const double*)b.F, b.ldF, b.prop, b.H, b.Hpart, b.hcnt);
+  if (b.mixed) {
+    const int nblk = hmat32_blocks(T);
+    k_hmat32<<<dim3(nblk, hmat32_splits(nblk)), 256, 0, s>>>(
+        b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma, (const float*)b.F, b.ldF, b.prop, b.H,
+        b.Hpart, b.hcnt);
+  } else {
+    const int nb = (T + 15) / 16;
+    const int ntile = nb * (nb + 1) / 2;
+    const int ks = hmat_splits(ntile, b.num_sms);
+    k_hmat<double><<<dim3(ntile, ks), 256, 0, s>>>(b.st, b.X, b.xld, b.d, b.kind, 1.0 / b.sigma,
+                                                   (const double*)b.F, b.ldF, b.prop, b.H,
+                                                   b.Hpart, b.hcnt);
+  }
   return cudaGetLastError();
 }
 

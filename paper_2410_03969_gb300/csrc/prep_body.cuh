@@ -30,6 +30,45 @@ namespace rpchol {
 // with the 64-byte swizzle (piece q of row j sits at q ^ ((j >> 1) & 3)).
 __device__ __forceinline__ int sw64_off(int j, int q) { return j * 64 + 16 * (q ^ ((j >> 1) & 3)); }
 
+// Piece q (8 columns) of chunk c of row j of the F image: FP16 head and
+// tail of -4096 F(S_j, 32 c + 8 q ..), zero beyond the rank or for padded
+// rows (frow null).
+__device__ __forceinline__ void prep_f_piece(const float* frow, long long rank, int j, int c, int q,
+                                             unsigned char* Bf, size_t cb, int s_pad) {
+  const long long col = 32ll * c + 8 * q;
+  float v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = (frow && col + e < rank) ? -4096.f * frow[col + e] : 0.f;
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const __half2 h = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+    hw[e] = *(const uint32_t*)&h;
+    lw[e] = *(const uint32_t*)&l;
+  }
+  unsigned char* base = Bf + (size_t)c * cb + sw64_off(j, q);
+  *(uint4*)base = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *(uint4*)(base + 64 * s_pad) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
+// Piece q (4 columns) of chunk c of row j of the X image: TF32 head and tail.
+__device__ __forceinline__ void prep_x_piece(const float* xrow, int j, int c, int q,
+                                             unsigned char* Bx, size_t cb, int s_pad) {
+  const int col = 16 * c + 4 * q;
+  float h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float v = xrow ? xrow[col + e] : 0.f;
+    h[e] = tc::tf32_head(v);
+    l[e] = v - h[e];
+  }
+  unsigned char* base = Bx + (size_t)c * cb + sw64_off(j, q);
+  *(float4*)base = make_float4(h[0], h[1], h[2], h[3]);
+  *(float4*)(base + 64 * s_pad) = make_float4(l[0], l[1], l[2], l[3]);
+}
+
 // Row j of the B images (one CTA per row).
 __device__ __forceinline__ void prep_row(const DevState* st, const float* F,
                                          long long ldF, const float* X, int xld,
@@ -47,40 +86,46 @@ __device__ __forceinline__ void prep_row(const DevState* st, const float* F,
   const int p = j < s ? Sacc[j] : -1;
   const float* frow = p >= 0 ? F + (long long)p * ldF : nullptr;
   const float* xrow = p >= 0 ? X + (long long)p * xld : nullptr;
-  for (int it = threadIdx.x; it < 4 * nF; it += blockDim.x) {
-    const int c = it >> 2, q = it & 3;
-    const long long col = 32ll * c + 8 * q;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = (frow && col + e < rank) ? -4096.f * frow[col + e] : 0.f;
-    uint32_t hw[4], lw[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const __half2 h = __floats2half2_rn(v[2 * e], v[2 * e + 1]);
-      const float2 hf = __half22float2(h);
-      const __half2 l = __floats2half2_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-      hw[e] = *(const uint32_t*)&h;
-      lw[e] = *(const uint32_t*)&l;
-    }
-    unsigned char* base = Bf + (size_t)c * cb + sw64_off(j, q);
-    *(uint4*)base = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *(uint4*)(base + 64 * s_pad) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  }
-  for (int it = threadIdx.x; it < 4 * nXc; it += blockDim.x) {
-    const int c = it >> 2, q = it & 3;
-    const int col = 16 * c + 4 * q;
-    float h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float v = xrow ? xrow[col + e] : 0.f;
-      h[e] = tc::tf32_head(v);
-      l[e] = v - h[e];
-    }
-    unsigned char* base = Bx + (size_t)c * cb + sw64_off(j, q);
-    *(float4*)base = make_float4(h[0], h[1], h[2], h[3]);
-    *(float4*)(base + 64 * s_pad) = make_float4(l[0], l[1], l[2], l[3]);
-  }
+  for (int it = threadIdx.x; it < 4 * nF; it += blockDim.x)
+    prep_f_piece(frow, rank, j, it >> 2, it & 3, Bf, cb, s_pad);
+  for (int it = threadIdx.x; it < 4 * nXc; it += blockDim.x)
+    prep_x_piece(xrow, j, it >> 2, it & 3, Bx, cb, s_pad);
   if (threadIdx.x == 0) nrmS[j] = p >= 0 ? nrm[p] : 0.f;
+}
+
+// Rows first, first + step, ... < s_pad of the B images in one pass of the
+// whole CTA (any thread count): the bytes prep_row writes for those rows.
+__device__ __forceinline__ void prep_rows_strided(const DevState* st, const float* F,
+                                                  long long ldF, const float* X, int xld,
+                                                  const float* nrm, const int* Sacc,
+                                                  unsigned char* Bf, unsigned char* Bx,
+                                                  float* nrmS, int first, int step) {
+  const int s = st->s;
+  if (s == 0) return;
+  const long long rank = st->rank;
+  const int s_pad = (s + 15) & ~15;
+  if (first >= s_pad) return;
+  const size_t cb = 128 * (size_t)s_pad;
+  const int nF = (int)((rank + 31) >> 5);
+  const int nXc = xld >> 4;
+  const int nrows = (s_pad - first + step - 1) / step;
+  const int per = 4 * nF + 4 * nXc;
+  for (int it = threadIdx.x; it < nrows * per; it += blockDim.x) {
+    const int r = it / per, k = it - r * per;
+    const int j = first + r * step;
+    const int p = j < s ? Sacc[j] : -1;
+    if (k < 4 * nF)
+      prep_f_piece(p >= 0 ? F + (long long)p * ldF : nullptr, rank, j, k >> 2, k & 3, Bf, cb,
+                   s_pad);
+    else
+      prep_x_piece(p >= 0 ? X + (long long)p * xld : nullptr, j, (k - 4 * nF) >> 2,
+                   (k - 4 * nF) & 3, Bx, cb, s_pad);
+  }
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    const int j = first + r * step;
+    const int p = j < s ? Sacc[j] : -1;
+    nrmS[j] = p >= 0 ? nrm[p] : 0.f;
+  }
 }
 
 // Blocked forward substitution operand for G L^* = R.  With the columns in
@@ -149,6 +194,52 @@ __device__ __forceinline__ void wblk(WblkSmem& S, const DevState* st,
   }
   if (part == 0)  // W_b(j0 + m, jj) = D_b^{-1}(jj, m)
     Wb[(long long)(j0 + r) * 16 + m] = (float)Dinv[m][r];
+}
+
+// All of W block b in one pass of 256 threads: D_b^{-1} once, then the
+// range l < j0 in pieces of 32 columns; every entry comes from the same
+// FP64 operations in the same order as in wblk, so the bytes are the same.
+__device__ __forceinline__ void wblk_full(WblkSmem& S, const DevState* st, const double* L,
+                                          int ldL, float* W, int b) {
+  double(&Db)[16][17] = S.Db;
+  double(&acc)[16][17] = S.acc;
+  double(&Dinv)[16][17] = S.Dinv;
+  double(&rdiag)[16] = S.rdiag;
+  double(&Lb)[16][33] = S.Lb;
+  const int s = st->s;
+  const int j0 = 16 * b;
+  if (j0 >= s) return;
+  const int t = threadIdx.x, r = t >> 4, m = t & 15;
+  auto Lat = [&](int rr, int cc) -> double {  // L with identity padding beyond s
+    if (rr >= s || cc >= s) return rr == cc ? 1.0 : 0.0;
+    return cc <= rr ? L[(long long)rr * ldL + cc] : 0.0;
+  };
+  Db[r][m] = Lat(j0 + r, j0 + m);
+  acc[r][m] = r == m ? 1.0 : 0.0;
+  if (t < 16) rdiag[t] = 1.0 / Lat(j0 + t, j0 + t);
+  body_sync();
+  for (int c = 0; c < 16; ++c) {
+    if (r >= c) {
+      const double xc = acc[c][m] * rdiag[c];
+      if (r == c) Dinv[c][m] = xc;
+      else acc[r][m] = fma(-Db[r][c], xc, acc[r][m]);
+    }
+    body_sync();
+  }
+  float* Wb = W + 256 * (long long)b * (b + 1) / 2;
+  for (int l0 = 0; l0 < j0; l0 += 32) {
+    const int nl = j0 - l0 < 32 ? j0 - l0 : 32;
+    for (int e = t; e < 16 * nl; e += 256) Lb[e / nl][e % nl] = Lat(j0 + e / nl, l0 + e % nl);
+    body_sync();
+    for (int e = t; e < 16 * nl; e += 256) {
+      const int l = e >> 4, jj = e & 15;
+      double a = 0.0;
+      for (int mm = 0; mm <= jj; ++mm) a = fma(Dinv[jj][mm], Lb[mm][l], a);
+      Wb[(long long)(l0 + l) * 16 + jj] = (float)(-a);
+    }
+    body_sync();
+  }
+  Wb[(long long)(j0 + r) * 16 + m] = (float)Dinv[m][r];
 }
 
 // One launch for both: CTAs [0, kTMax) prepare the rows of the B operands,

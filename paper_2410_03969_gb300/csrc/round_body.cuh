@@ -325,6 +325,169 @@ __device__ __forceinline__ void hmat_body(int tile, int z, int KS, TF (*Fa)[33],
   }
 }
 
+// H for an FP32 factor (mixed mode).  Output blocks of 32 x 32 (lower
+// triangle of blocks), 256 threads, each thread four entries (rows a0 + ty
+// + 16 i, columns b0 + tx + 16 j), so that four independent accumulations
+// hide the latency of each.  The products of FP32 entries are summed as
+// unevaluated float pairs (exact product by FMA, two-sum of Knuth) on the
+// FP32 pipe, which on this GPU issues far more than the FP64 one; about 48
+// bits survive, well below the FP32 rounding of F itself.  The rank
+// dimension is split KS ways (hmat32_splits), each split writes its partial
+// sums, and the last split of a block to finish (counted with an atomic)
+// adds the KS partials in the fixed order z = 0..KS-1, so the result does
+// not depend on timing or on which CTA runs which split.  The kernel
+// entries of a block (FP64) are shared out among its KS splits.
+__host__ __device__ __forceinline__ int hmat32_blocks(int T) {
+  const int nb = (T + 31) / 32;
+  return nb * (nb + 1) / 2;
+}
+__host__ __device__ __forceinline__ int hmat32_splits(int nblk) {
+  int ks = (32 + nblk - 1) / nblk;
+  if (ks > kHSplitMax) ks = kHSplitMax;
+  return ks < 1 ? 1 : ks;
+}
+
+struct H32Smem {
+  float Fa[32][33];
+  float Fb[32][33];
+  int last;
+};
+
+__device__ __forceinline__ void dfloat_acc(float& sh, float& sl, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = fmaf(a, b, -p);
+  const float t = __fadd_rn(sh, p);
+  const float bp = __fsub_rn(t, sh);
+  const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(er, e));
+}
+
+// One block (blk, z) of H for an FP32 factor: lower block `blk` (row-major
+// over (ta, tb), tb <= ta), rank split z of KS; 256 threads.
+__device__ __forceinline__ void hmat32_body(int blk, int z, int KS, H32Smem& S, const DevState* st,
+                                            const float* X, int xld, int d, int kind,
+                                            double inv_sigma, const float* F, long long ldF,
+                                            const int* prop, double* H, double* Hpart,
+                                            int* hcnt) {
+  if (st->done) return;
+  const int T = st->T;
+  const long long rank = st->rank;
+  int ta = (int)((sqrtf(8.f * blk + 1.f) - 1.f) * 0.5f);
+  while ((ta + 1) * (ta + 2) / 2 <= blk) ++ta;
+  while (ta * (ta + 1) / 2 > blk) --ta;
+  const int tb = blk - ta * (ta + 1) / 2;
+  const int a0 = 32 * ta, b0 = 32 * tb;
+  if (a0 >= T) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long long kc = (rank + KS - 1) / KS;
+  const long long m_lo = z * kc < rank ? z * kc : rank;
+  const long long m_hi = m_lo + kc < rank ? m_lo + kc : rank;
+  // staged elements: row (tid >> 5) + 8 q, column tid & 31, q = 0..3
+  const int cc = tid & 31;
+  int ra[4], rb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = (tid >> 5) + 8 * q;
+    ra[q] = a0 + r < T ? prop[a0 + r] : prop[0];
+    rb[q] = b0 + r < T ? prop[b0 + r] : prop[0];
+  }
+  float va[4], vb[4];  // the next chunk, loaded while the current one is used
+  auto fetch = [&](long long m0) {
+    const long long m = m0 + cc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      va[q] = m < m_hi ? F[(long long)ra[q] * ldF + m] : 0.f;
+      vb[q] = m < m_hi ? F[(long long)rb[q] * ldF + m] : 0.f;
+    }
+  };
+  // kernel entry of H at (a, b), 1 on the diagonal of A
+  auto kval = [&](int a, int b) -> double {
+    const int pa = prop[a], pb = prop[b];
+    if (pa == pb) return 1.0;
+    const float* xa = X + (long long)pa * xld;
+    const float* xb = X + (long long)pb * xld;
+    double r2 = 0.0;
+    for (int l = 0; l < d; ++l) {
+      const double t = (double)xa[l] - (double)xb[l];
+      r2 += dist_term(kind, t);
+    }
+    return phi_r2<double>(kind, inv_sigma, r2);
+  };
+  if (m_lo < m_hi) fetch(m_lo);
+  double* P = Hpart + (long long)blk * (KS + 1) * 1024;
+  if (KS > 1) {
+    // this split's share of the kernel entries, formed while the first
+    // chunk of F is in flight
+    for (int e = z + KS * tid; e < 1024; e += KS * 256) {
+      const int a = a0 + (e >> 5), bb = b0 + (e & 31);
+      if (a < T && bb < T && bb <= a) P[KS * 1024 + e] = kval(a, bb);
+    }
+  }
+  float sh[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, sl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (long long m0 = m_lo; m0 < m_hi; m0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = (tid >> 5) + 8 * q;
+      S.Fa[r][cc] = va[q];
+      S.Fb[r][cc] = vb[q];
+    }
+    body_sync();
+    if (m0 + 32 < m_hi) fetch(m0 + 32);
+    const int qn = m_hi - m0 < 32 ? (int)(m_hi - m0) : 32;
+#pragma unroll 4
+    for (int q = 0; q < qn; ++q) {
+      const float x0 = S.Fa[ty][q], x1 = S.Fa[ty + 16][q];
+      const float y0 = S.Fb[tx][q], y1 = S.Fb[tx + 16][q];
+      dfloat_acc(sh[0][0], sl[0][0], x0, y0);
+      dfloat_acc(sh[0][1], sl[0][1], x0, y1);
+      dfloat_acc(sh[1][0], sl[1][0], x1, y0);
+      dfloat_acc(sh[1][1], sl[1][1], x1, y1);
+    }
+    body_sync();
+  }
+  double sum[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) sum[i][j] = (double)sh[i][j] + (double)sl[i][j];
+  if (KS > 1) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) P[z * 1024 + (ty + 16 * i) * 32 + tx + 16 * j] = sum[i][j];
+    __threadfence();
+    body_sync();
+    if (tid == 0) S.last = atomicAdd(&hcnt[blk], 1) == KS - 1;
+    body_sync();
+    if (!S.last) return;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int e = (ty + 16 * i) * 32 + tx + 16 * j;
+        double t = 0.0;
+        for (int zz = 0; zz < KS; ++zz) t += __ldcg(P + zz * 1024 + e);
+        sum[i][j] = t;
+      }
+    if (tid == 0) hcnt[blk] = 0;
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = a0 + ty + 16 * i, bcol = b0 + tx + 16 * j;
+      if (a < T && bcol < T && bcol <= a) {
+        const int e = (ty + 16 * i) * 32 + tx + 16 * j;
+        const double kv = KS > 1 ? __ldcg(P + KS * 1024 + e) : kval(a, bcol);
+        const double h = kv - sum[i][j];
+        H[(long long)a * T + bcol] = h;
+        H[(long long)bcol * T + a] = h;
+      }
+    }
+}
+
 // ------------------------------------------------------------------ Algorithm 1
 // RejectionSampleSubmatrix.  For i = 0..T-1: accept iff u_i * U_i < h_ii
 // (u_i the proposal weight d[s'_i], h_ii the current Schur diagonal); on

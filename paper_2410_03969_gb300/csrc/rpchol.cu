@@ -502,7 +502,7 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
   ALLOC(L, double, (size_t)kTMax * T_max);
   ALLOC(Linv, double, (size_t)kTMax * T_max);
   ALLOC(Sacc, int, kTMax);
-  ALLOC(Hpart, double, (size_t)kHTilesMax * (kHSplitMax + 1) * 256);
+  ALLOC(Hpart, double, (size_t)kHPartDoubles);
   ALLOC(hcnt, int, kHTilesMax);
   ALLOC(ccnt, unsigned, 1);
   ALLOC(red, double, b.nred);
@@ -1025,7 +1025,7 @@ int64_t rpchol_context_bytes(int64_t N, int32_t d, int64_t k_max, int32_t T_max,
   b += bf * N * ldF;                                  // F
   b += 8 * k_max + 4 * kTMax + 16 * kTMax + 4 * kTMax;  // pivots, proposals, uniforms
   b += 8 * 2LL * kTMax * kTMax + 8 * 2LL * kTMax * T_max;  // H, Lw, L, Linv
-  b += 8LL * kHTilesMax * (kHSplitMax + 1) * 256 + 4 * kHTilesMax + 4;  // H partials, counters
+  b += 8LL * kHPartDoubles + 4 * kHTilesMax + 4;  // H partials, counters
   b += 8 * (2 + 2048 + 2) + (long long)sizeof(DevState);
   b += 8LL * T_max * (ldF + kTMax);                   // extended operand rows
   if (mixed && N >= 128) {
