@@ -72,15 +72,22 @@ def _peaks():
 
 
 # DRAM traffic of the tensor-core column step per launch (dram__bytes_read.sum +
-# dram__bytes_write.sum of every k_colstep_tc launch of one ncu capture of
-# `bench.py --quick --no-graph --steps 1 --warmup 1` on this workload, divided
-# by the number of launches), with the SHA-256 of the sources the capture ran.
-# When those sources have changed since, the figure no longer describes the
-# kernel and the bench reports null.  Summary: profiles/colstep_tc_mixture20_n1e5.md.
-_COLSTEP_SOURCES = ("k_colstep_tc.cu", "tc_ptx.cuh", "common.cuh", "internal.h")
+# dram__bytes_write.sum of the k_colstep_tc launches of one ncu capture of
+# `bench.py --quick --no-graph --steps 1 --warmup 1` on the workload, averaged over
+# the launches that ran a round), with the SHA-256 of the sources the capture ran.
+# The N = 10^6 workload (16 GB of F) is captured at N = 10^5 (`--n-points 100000`,
+# same k, T and rank sequence) and scaled by the rows, 10x: every row of F and X is
+# read once per round, so the traffic grows in proportion to N.  When the sources
+# have changed since, the figure no longer describes the kernel and the bench
+# reports null.  Summaries: profiles/colstep_tc_unif64_n1e6.md (and
+# profiles/colstep_tc_mixture20_n1e5.md for the earlier kernel).
+_COLSTEP_SOURCES = ("k_colstep_tc.cu", "colstep_body.cuh", "tc_ptx.cuh", "common.cuh",
+                    "internal.h")
 _COLSTEP_TRAFFIC = {
     ("mixture20_n1e5", "mixed"): (
         162153888.0, "04fcd24dcced58aeb93d85712943709620fd5bdf030f42de1d6c007425f931cb"),
+    ("unif64_n1e6", "mixed"): (
+        8925080543.0, "8222347ebc35195dcde9f078fff6a2dd79bfe920f1d340dbb1a5ed331d79fbb6"),
 }
 
 
