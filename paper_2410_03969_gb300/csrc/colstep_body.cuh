@@ -33,17 +33,21 @@
 // tile each).  Warp roles (384 threads):
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
-//   warps 2-3   convert each FP32 F chunk in shared memory, in place, into
-//               FP16 head and tail (interleaved 8-row swizzle atoms)
+//   warps 2-3   no role in the column step (the CTA shape the batch engine
+//               shares)
 //   warps 4-11  epilogue: two groups of four warps taking alternate tiles,
 //               warp 4 + q (8 + q) reading TMEM lane quarter q, 4 rows per
 //               thread.
 // Operands stream through a ring of shared-memory stages, each a 16 KiB A
-// region (128 rows x 128 bytes) and a B region of 2 x s_pad rows x 64
-// bytes.  A stage holds one chunk: 16 coordinates of X (TF32 head and tail
-// planes, by TMA, 64-byte swizzle) against the same 16 of X_S, or 32
-// columns of F (FP32 by TMA, converted in place into 64-byte-swizzled FP16
-// head and tail) against the same 32 of F(S,:).  The B operands of the
+// region (two planes of 128 rows x 64 bytes) and a B region of 2 x s_pad
+// rows x 64 bytes.  A stage holds one chunk: 16 coordinates of X (TF32 head
+// and tail planes) against the same 16 of X_S, or 32 columns of F (FP16
+// heads and tails of 4096 F, which the epilogue writes beside F with
+// every new column) against the same 32 of F(S,:).  Both A operands arrive by
+// TMA ready for the MMAs: X as two planes with the 64-byte swizzle; F as
+// one 128-row box of 128-byte rows (per row the 32 heads, then the 32
+// tails, stored so in HBM) with the 128-byte swizzle, whose head and tail
+// halves the MMAs address as K offsets 0 and 64 bytes.  The B operands of the
 // round are laid out by the operand-prep kernel as the exact shared-memory
 // image of each chunk and arrive with one bulk copy per chunk.  The
 // producer streams the next tile's X chunks inside the current tile's F
@@ -80,7 +84,13 @@ constexpr int kSmallBytes = 4 * 1024;     // pivots, their norms, barriers, flag
 constexpr int kTailBytes = 256;
 constexpr int kMaxStages = 6;
 constexpr int kMaxBuf = 4;                // tiles held in TMEM at once
-constexpr int kPrefetch = 8;              // chunks prefetched into L2 ahead of their loads
+#ifndef RPCHOL_COLSTEP_PREFETCH
+#define RPCHOL_COLSTEP_PREFETCH 8
+#endif
+#ifndef RPCHOL_COLSTEP_W_RESIDENT
+#define RPCHOL_COLSTEP_W_RESIDENT 1
+#endif
+constexpr int kPrefetch = RPCHOL_COLSTEP_PREFETCH;  // chunks prefetched into L2 ahead of their loads
 constexpr float kFScale = 4096.f;         // the Schur operands are heads/tails of 4096 F
 constexpr float kAccScale = 16777216.f;   // 4096^2: the scale of the Schur products
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
@@ -107,7 +117,7 @@ __host__ __device__ inline Layout make_layout(int s) {
   int st_w = (budget - wbytes) / L.stage_bytes;
   if (st_w > kMaxStages) st_w = kMaxStages;
   const int want = st_nw < 3 ? st_nw : 3;
-  L.w_resident = st_w >= want ? 1 : 0;
+  L.w_resident = (RPCHOL_COLSTEP_W_RESIDENT && st_w >= want) ? 1 : 0;
   L.stages = L.w_resident ? st_w : st_nw;
   L.w_off = L.stages * L.stage_bytes;
   L.small_off = L.w_off + (L.w_resident ? wbytes : 0);
@@ -122,8 +132,8 @@ __host__ __device__ inline Layout make_layout(int s) {
 // or more tiles in TMEM split = 0 (the next tile's distances and kappa pass
 // run while this tile's Schur MMAs execute); with two, the next tile's
 // buffer frees only when the epilogue of tile t - 1 is done, so its X chunks
-// come two thirds of the way through tile t's F chunks.  Producer, converter
-// and MMA issuer walk the same sequence.
+// come two thirds of the way through tile t's F chunks.  Producer and MMA
+// issuer walk the same sequence.
 struct Seq {
   int t, ph, c;  // ph 0: F(t) before the split, 1: X(t + 1), 2: F(t) after it
   int ntl, nXc, nF, nFi, split;
@@ -175,10 +185,12 @@ struct EpiQuad {
   const float* W;        // W blocks of the round
   const float* nrmSs;    // squared norms of the round's pivots
   const double* L;       // FP64 Cholesky factor of the round
-  float* frow[4];        // F(row ri, rank), nullptr beyond N
+  long long fidx[4];     // element index of F(row ri, rank), -1 beyond N
+  float* F;              // the factor, FP32
+  __half* Fs;            // FP16 heads / tails of 4096 F, interleaved by 32-column chunk
   float nr[4];           // squared norms of the rows
   int jpiv[4];           // index among the round's pivots, or -1
-  int s, kind, ldL, cq, lane, even;
+  int s, kind, ldL, cq, lane, even, rank31;
   float inv_sigma;
 };
 
@@ -312,16 +324,35 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
     tc::tmem_st_quad16(e.acc + j0, G);  // G_b over the consumed R block
 #pragma unroll
     for (int ri = 0; ri < 4; ++ri) {
-      if (e.frow[ri]) {
+      if (e.fidx[ri] >= 0) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           const int col = j0 + 8 * g + 2 * cq;
-          float* dst = e.frow[ri] + col;
+          const long long idx = e.fidx[ri] + col;  // F(row, rank + col)
+          // the FP16 head and tail of 4096 G, as later rounds' Schur MMAs
+          // read them: head of F(r, c) at 2 (r ldF + c) - (c mod 32), its
+          // tail 32 further
+          const long long hidx = 2 * idx - ((e.rank31 + col) & 31);
+          const float y0 = G[ri][2 * g] * kFScale, y1 = G[ri][2 * g + 1] * kFScale;
+          const __half2 h = __floats2half2_rn(y0, y1);
+          const float2 hf = __half22float2(h);
+          const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
           if (e.even && col + 1 < e.s) {
-            *(float2*)dst = make_float2(G[ri][2 * g], G[ri][2 * g + 1]);
+            *(float2*)(e.F + idx) = make_float2(G[ri][2 * g], G[ri][2 * g + 1]);
+            *(__half2*)(e.Fs + hidx) = h;
+            *(__half2*)(e.Fs + hidx + 32) = l;
           } else {
-            if (col < e.s) dst[0] = G[ri][2 * g];
-            if (col + 1 < e.s) dst[1] = G[ri][2 * g + 1];
+            if (col < e.s) {
+              e.F[idx] = G[ri][2 * g];
+              e.Fs[hidx] = __low2half(h);
+              e.Fs[hidx + 32] = __low2half(l);
+            }
+            if (col + 1 < e.s) {
+              const long long hidx1 = 2 * (idx + 1) - ((e.rank31 + col + 1) & 31);
+              e.F[idx + 1] = G[ri][2 * g + 1];
+              e.Fs[hidx1] = __high2half(h);
+              e.Fs[hidx1 + 32] = __high2half(l);
+            }
           }
         }
       }
@@ -336,48 +367,12 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
   }
 }
 
-// In-place conversion of an FP32 F chunk (16 KiB: 128 rows of 32 floats as
-// TMA wrote them, 128-byte swizzle) into the FP16 head and tail of 4096 x.
-// Each 8-row group g (1 KiB at 1024 g) becomes its head rows (the first 512
-// bytes) and tail rows (the next 512), each an 8-row atom of the 64-byte
-// swizzle.  Warp w takes groups w, w + 2, ..., w + 14; lane l takes row
-// l / 4 of a group, floats 8 (l % 4) .. 8 (l % 4) + 7.  All eight groups are
-// read before any write (the reads and writes of a group overlap in place).
-// Both patterns touch eight distinct 16-byte bank groups per quarter warp.
-__device__ __forceinline__ void convert_chunk(unsigned char* sA, int w, int lane) {
-  const int i = lane >> 2, q = lane & 3;
-  float4 va[8], vb[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const unsigned char* grp = sA + 1024 * (w + 2 * u);
-    va[u] = *(const float4*)(grp + i * 128 + 16 * ((2 * q) ^ i));
-    vb[u] = *(const float4*)(grp + i * 128 + 16 * ((2 * q + 1) ^ i));
-  }
-  __syncwarp();
-  const int pos = 16 * (q ^ ((i >> 1) & 3));
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const float x[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
-    uint32_t hw[4], lw[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float y0 = x[2 * p] * kFScale, y1 = x[2 * p + 1] * kFScale;
-      const __half2 h = __floats2half2_rn(y0, y1);
-      const float2 hf = __half22float2(h);
-      const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
-      hw[p] = *(const uint32_t*)&h;
-      lw[p] = *(const uint32_t*)&l;
-    }
-    unsigned char* grp = sA + 1024 * (w + 2 * u);
-    *(uint4*)(grp + i * 64 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *(uint4*)(grp + 512 + i * 64 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-  }
-}
 }  // namespace
 
 struct TcArgs {
   DevState* st;
   float* F;
+  __half* Fs;               // FP16 heads / tails of 4096 F, written with F
   long long ldF;
   long long N;
   const float* nrm;         // ||x||^2, FP32
@@ -406,6 +401,7 @@ inline TcArgs make_tc_args(const TcMaps& m, const DevBuffers& b, unsigned long l
   TcArgs a;
   a.st = b.st;
   a.F = (float*)b.F;
+  a.Fs = (__half*)m.Fsp;
   a.ldF = b.ldF;
   a.N = b.N;
   a.nrm = b.nrm;
@@ -432,12 +428,19 @@ inline TcArgs make_tc_args(const TcMaps& m, const DevBuffers& b, unsigned long l
 // The column step of one round on CTA `cta` of `ncta` (tiles cta, cta +
 // ncta, ...), with 4 + 4 g warps (g epilogue groups), shared memory at sm
 // (1024-byte aligned, kSmemMax bytes) and 512 TMEM columns at tbase
-// allocated by the caller.  The last of the ncta CTAs to finish closes the
-// round; the one thread that closed it gets true.
-__device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUtensorMap* tmXh,
-                                             const CUtensorMap* tmXl, const TcArgs& a,
+// allocated by the caller.  With mc > 1 the CTAs cta - cta % mc .. + mc - 1
+// are one thread-block cluster (cluster rank cta % mc) that shares each B
+// operand: every CTA loads 1/mc of it into all of them (bulk-copy
+// multicast), a stage is refilled once all mc CTAs' MMAs are done with it
+// (multicast commits), and all walk the same number of tiles (a CTA past
+// the last tile streams zero rows and writes nothing).  The last of the
+// ncta CTAs to finish closes the round; the one thread that closed it gets
+// true.
+__device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUtensorMap* tmXh,
+                                             const CUtensorMap* tmXl,
+                                             const TcArgs& a,
                                              unsigned char* sm, uint32_t tbase, int cta,
-                                             int ncta) {
+                                             int ncta, int mc = 1) {
   DevState* st = a.st;
   // a round that ended early (nothing accepted, or the run is done) is
   // closed by one thread; otherwise the last CTA to finish closes it
@@ -456,7 +459,10 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
   const int nXc = a.xld / kXK;
   const int nF = (int)((rank + kFK - 1) / kFK);
   const long long ntiles = (a.N + kBM - 1) / kBM;
-  const int ntl = (int)((ntiles - cta + ncta - 1) / ncta);
+  const int crank = cta % mc;                       // rank in the multicast cluster
+  const uint16_t mc_mask = (uint16_t)((1u << mc) - 1u);
+  // tiles of the cluster's first CTA: every CTA of the cluster walks as many
+  const int ntl = (int)((ntiles - (cta - crank) + ncta - 1) / ncta);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ngroups = ((int)(blockDim.x >> 5) - 4) >> 2;  // epilogue groups of four warps
 
@@ -464,8 +470,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
   int* Ss = (int*)small;                       // [256] pivots of the round (-1 beyond s)
   float* nrmSs = (float*)(small + 1024);       // [256] their squared norms
   uint64_t* full = (uint64_t*)(small + 2048);  // [kMaxStages] A operand landed
-  uint64_t* conv = full + kMaxStages;          // [kMaxStages] A ready for the MMAs
-  uint64_t* empty = conv + kMaxStages;         // [kMaxStages]
+  uint64_t* empty = full + 2 * kMaxStages;     // [kMaxStages]
   uint64_t* fullB = empty + kMaxStages;        // [kMaxStages] B operand landed
   uint64_t* d1f = fullB + kMaxStages;          // [kMaxBuf] distance MMAs of a tile done
   uint64_t* midf = d1f + kMaxBuf;              // [kMaxBuf] kappa pass of a tile done
@@ -490,8 +495,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
     for (int i = 0; i < NS; ++i) {
       tc::mbar_init(&full[i], 1);
       tc::mbar_init(&fullB[i], 1);
-      tc::mbar_init(&conv[i], 2);  // one arrival per converter warp
-      tc::mbar_init(&empty[i], 1);
+      tc::mbar_init(&empty[i], (uint32_t)mc);  // one MMA commit per CTA of the cluster
     }
     for (int i = 0; i < kMaxBuf; ++i) {
       tc::mbar_init(&d1f[i], 1);
@@ -504,12 +508,13 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
   }
   tc::cp_async_wait<0>();
   __syncthreads();
+  if (mc > 1) tc::cluster_barrier();  // every barrier of the cluster is initialised
   tc::tc_fence_after();
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
-      tc::prefetch_tmap(tmF);
+      tc::prefetch_tmap(tmFs);
       tc::prefetch_tmap(tmXh);
       tc::prefetch_tmap(tmXl);
       // The A operands (rows of F and X, read once per round from HBM) are
@@ -525,7 +530,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
           tc::tma_prefetch_2d(tmXh, pf.c * kXK, prow);
           tc::tma_prefetch_2d(tmXl, pf.c * kXK, prow);
         } else {
-          tc::tma_prefetch_2d(tmF, pf.c * kFK, prow);
+          tc::tma_prefetch_2d(tmFs, pf.c * 2 * kFK, prow);
         }
         pf.next();
       };
@@ -543,17 +548,32 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
         unsigned char* sA = sm + stg * SB;
         unsigned char* sB = sA + kStageA;
         tc::mbar_arrive_expect_tx(&full[stg], (uint32_t)kStageA);
-        tc::mbar_arrive_expect_tx(&fullB[stg], bbytes);
+        tc::mbar_arrive_expect_tx(&fullB[stg], bbytes);  // all mc slices land here
         if (kd == 0) {
           tc::tma_load_2d(sA, tmXh, sq.c * kXK, row0, &full[stg]);
           tc::tma_load_2d(sA + kStageA / 2, tmXl, sq.c * kXK, row0, &full[stg]);
-          tc::bulk_load(sB, a.Bx + (size_t)sq.c * bbytes, bbytes, &fullB[stg]);
         } else {
-          tc::tma_load_2d(sA, tmF, sq.c * kFK, row0, &full[stg]);
-          tc::bulk_load(sB, a.Bf + (size_t)sq.c * bbytes, bbytes, &fullB[stg]);
+          tc::tma_load_2d(sA, tmFs, sq.c * 2 * kFK, row0, &full[stg]);
+        }
+        const unsigned char* srcB = (kd == 0 ? a.Bx : a.Bf) + (size_t)sq.c * bbytes;
+        if (mc == 1) {
+          tc::bulk_load(sB, srcB, bbytes, &fullB[stg]);
+        } else {
+          const uint32_t sl = bbytes / (uint32_t)mc;  // a multiple of 512
+          tc::bulk_load_mc(sB + crank * sl, srcB + crank * sl, sl, &fullB[stg], mc_mask);
         }
         ++g;
-        prefetch_next();
+        if (kPrefetch > 0) prefetch_next();
+      }
+      if (mc > 1 && !*abort_flag) {
+        // the last stages' releases by the other CTAs (multicast commits)
+        // must have landed before this CTA's barriers are invalidated
+        for (long long q = (g > NS ? g - NS : 0); q < g; ++q)
+          if (!tc::mbar_wait_bounded(&empty[q % NS], (uint32_t)((q / NS) & 1), kWaitNs,
+                                     abort_flag)) {
+            atomicOr(a.err, (int)kStTimeout);
+            break;
+          }
       }
       if (*abort_flag) {
         // drain: the (at most NS) issued loads not yet consumed must land
@@ -589,7 +609,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
         }
         const int stg = (int)(g % NS);
         const uint32_t ph = (uint32_t)((g / NS) & 1);
-        if (!tc::mbar_wait_bounded(&conv[stg], ph, kWaitNs, abort_flag) ||
+        if (!tc::mbar_wait_bounded(&full[stg], ph, kWaitNs, abort_flag) ||
             !tc::mbar_wait_bounded(&fullB[stg], ph, kWaitNs, abort_flag))
           break;
         tc::tc_fence_after();
@@ -609,44 +629,31 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
             tc::mma_tf32_reuse_a(acc, da, dbl, id32, 1u);
             tc::mma_tf32(acc, dal, dbh, id32, 1u);
           }
-          tc::mma_commit(&empty[stg]);
+          if (mc == 1) tc::mma_commit(&empty[stg]);
+          else tc::mma_commit_mc(&empty[stg], mc_mask);
           if (sq.c == nXc - 1) tc::mma_commit(&d1f[b]);
         } else {
-          // F head / tail in interleaved 512-byte atoms, FP16, K = 16 per MMA
+          // FP16 heads (bytes 0-63 of each 128-byte row) and tails (64-127) of
+          // 4096 F, 128-byte swizzle, K = 16 per MMA
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t da = tc::smem_desc(aA + 32 * kk, 1024, 4);
-            const uint64_t dal = tc::smem_desc(aA + 512 + 32 * kk, 1024, 4);
+            const uint64_t da = tc::smem_desc(aA + 32 * kk, 1024, 2);
+            const uint64_t dal = tc::smem_desc(aA + 64 + 32 * kk, 1024, 2);
             const uint64_t dbh = tc::smem_desc(aB + 32 * kk, 512, 4);
             const uint64_t dbl = tc::smem_desc(aBl + 32 * kk, 512, 4);
             tc::mma_f16_keep_a(acc, da, dbh, id16, 1u);
             tc::mma_f16_reuse_a(acc, da, dbl, id16, 1u);
             tc::mma_f16(acc, dal, dbh, id16, 1u);
           }
-          tc::mma_commit(&empty[stg]);
+          if (mc == 1) tc::mma_commit(&empty[stg]);
+          else tc::mma_commit_mc(&empty[stg], mc_mask);
           if (sq.c == nF - 1) tc::mma_commit(&accf[b]);
         }
         ++g;
       }
     }
   } else if (warp < 4) {
-    // ------------------------------------------------ in-place FP16 split of F chunks
-    const int w = warp - 2;
-    long long g = 0;
-    Seq sq;
-    for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
-      const int kd = sq.kind();
-      if (kd == 2) continue;
-      const int stg = (int)(g % NS);
-      if (!tc::mbar_wait_warp(&full[stg], (uint32_t)((g / NS) & 1), kWaitNs, abort_flag)) break;
-      if (kd == 1) {
-        unsigned char* sA = sm + stg * SB;
-        convert_chunk(sA, w, lane);
-        tc::fence_proxy_async_smem();
-      }
-      tc::mbar_arrive_warp(&conv[stg]);
-      ++g;
-    }
+    // no role in the column step
   } else {
     // ------------------------------------------------ epilogue: groups of four
     // warps take alternate tiles
@@ -669,7 +676,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
       for (int ri = 0; ri < 4; ++ri) {
         growv[ri] = row0 + 32 * q + (lane >> 2) + 16 * (ri >> 1) + 8 * (ri & 1);
         const bool lv = growv[ri] < a.N;
-        eq.frow[ri] = lv ? a.F + growv[ri] * a.ldF + rank : nullptr;
+        eq.fidx[ri] = lv ? growv[ri] * a.ldF + rank : -1;
         eq.nr[ri] = lv ? a.nrm[growv[ri]] : 0.f;
         eq.jpiv[ri] = -1;
       }
@@ -684,6 +691,9 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
           if (p == growv[ri]) eq.jpiv[ri] = jj;
       }
       eq.acc = tbase + lane_off + (uint32_t)(b * Lo.s_alloc);
+      eq.F = a.F;
+      eq.Fs = a.Fs;
+      eq.rank31 = (int)(rank & 31);
       eq.W = Lo.w_resident ? Wsm : a.W;
       eq.nrmSs = nrmSs;
       eq.L = a.L;
@@ -746,7 +756,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
       for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);
       if (lane == 0) red[grp * 4 + q] = dn;
       asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
-      if (gt == 0)
+      if (gt == 0 && tile < ntiles)
         a.tile_sums[tile] = red[grp * 4] + red[grp * 4 + 1] + red[grp * 4 + 2] + red[grp * 4 + 3];
     }
   }
@@ -755,13 +765,13 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmF, const CUten
   // copies (async proxy)
   tc::fence_proxy_async_all();
   __syncthreads();
+  if (mc > 1) tc::cluster_barrier();  // no CTA's copies or commits still reach another
   bool closed = false;
   if (threadIdx.x == 0) {
     // the barriers' shared memory goes back to other uses
     for (int i = 0; i < NS; ++i) {
       tc::mbar_inval(&full[i]);
       tc::mbar_inval(&fullB[i]);
-      tc::mbar_inval(&conv[i]);
       tc::mbar_inval(&empty[i]);
     }
     for (int i = 0; i < kMaxBuf; ++i) {

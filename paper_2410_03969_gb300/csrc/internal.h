@@ -12,8 +12,10 @@ namespace rpchol {
 
 // Tensor maps and buffers of the tensor-core column step (mixed mode).
 struct TcMaps {
-  CUtensorMap F;        // F, box 32 x 128, 128-byte swizzle
+  CUtensorMap Fs;       // FP16 heads / tails of 4096 F, box 64 x 128, 128-byte swizzle
   CUtensorMap Xh, Xl;   // TF32 head / tail planes of X, box 16 x 128, 64-byte swizzle
+  void* Fsp;            // N x 2 ldF FP16: row r, 32-column chunk c at 64 c holds the 32
+                        // heads, then the 32 tails; written with every column of F
   float* Xhp;
   float* Xlp;
   unsigned char* Bf;    // (ldF / 32) chunk images of F(S,:), 128 x kTMax bytes each
@@ -26,6 +28,10 @@ struct TcMaps {
 
 cudaError_t launch_prep_tc(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
 cudaError_t launch_split_x(const TcMaps& m, const struct DevBuffers& b, cudaStream_t s);
+// FP16 heads / tails of columns [0, cols) of F from the FP32 factor
+// (after a checkpoint restore; the column step writes them with F otherwise)
+cudaError_t launch_f16_planes(const TcMaps& m, const struct DevBuffers& b, long long cols,
+                              cudaStream_t s);
 // The tensor-core column step also closes the round (see round_end_body):
 // `cond` / `use_cond` as for launch_round_end.
 cudaError_t launch_colstep_tc(const TcMaps& m, const struct DevBuffers& b, unsigned long long cond,

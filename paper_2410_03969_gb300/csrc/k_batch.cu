@@ -58,7 +58,7 @@ struct EngineInst {
 
 // The instance's tensor maps (device memory; CUtensorMap is 64-byte aligned).
 struct EngineMaps {
-  CUtensorMap F, Xh, Xl;
+  CUtensorMap Fs, Xh, Xl;
 };
 
 // Scheduler state (device memory, zeroed before every launch): the header,
@@ -380,7 +380,7 @@ __global__ void __cluster_dims__(kEngCluster, 1, 1) __launch_bounds__(kEngThread
       const int ii = order[J.slot];
       // the operand images and F were written by generic stores elsewhere
       tc::fence_proxy_async_all();
-      const bool closed = colstep_body(&maps[ii].F, &maps[ii].Xh, &maps[ii].Xl, insts[ii].ta, sm,
+      const bool closed = colstep_body(&maps[ii].Fs, &maps[ii].Xh, &maps[ii].Xl, insts[ii].ta, sm,
                                        tbase, J.part, J.parts);
       if (closed) after_round_end(q, slots, J.slot, insts[ii].b.st);
     }
@@ -432,7 +432,7 @@ cudaError_t engine_setup(int n, const DevBuffers* bs, const TcMaps* ms, void** i
   for (int i = 0; i < n; ++i) {
     hi[i].b = bs[i];
     hi[i].ta = make_tc_args(ms[i], bs[i], 0ull, 0);
-    hm[i].F = ms[i].F;
+    hm[i].Fs = ms[i].Fs;
     hm[i].Xh = ms[i].Xh;
     hm[i].Xl = ms[i].Xl;
   }

@@ -13,7 +13,8 @@
 //   - the blocked-substitution operand W built from the round's compact
 //     Cholesky factor L in FP64 and rounded once to FP32 (wblk below), in
 //     the same launch.
-// Also the one-time split of X into TF32 head and tail planes.
+// Also the one-time split of X into TF32 head and tail planes, and the FP16
+// planes of F after a checkpoint restore.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -40,6 +41,30 @@ __global__ void k_split_x(const float* __restrict__ X, long long n, float* Xh, f
   const float h = tc::tf32_head(v);
   Xh[i] = h;
   Xl[i] = v - h;
+}
+
+// FP16 head and tail of 4096 F(r, c), c < cols: the split the epilogue of
+// the column step writes with every column (same operations, same place:
+// the head at 2 (r ldF + c) - (c mod 32), the tail 32 further)
+__global__ void k_f16_planes(const float* __restrict__ F, long long ldF, long long N,
+                             long long cols, __half* Fs) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * cols) return;
+  const long long r = i / cols, c = i - r * cols;
+  const float y = F[r * ldF + c] * 4096.f;
+  const __half h = __float2half_rn(y);
+  const long long hi = 2 * (r * ldF + c) - (c & 31);
+  Fs[hi] = h;
+  Fs[hi + 32] = __float2half_rn(y - __half2float(h));
+}
+
+cudaError_t launch_f16_planes(const TcMaps& m, const DevBuffers& b, long long cols,
+                              cudaStream_t s) {
+  if (cols <= 0) return cudaSuccess;
+  const long long n = b.N * cols;
+  k_f16_planes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)b.F, b.ldF, b.N, cols,
+                                                          (__half*)m.Fsp);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep_tc(const TcMaps& m, const DevBuffers& b, cudaStream_t s) {

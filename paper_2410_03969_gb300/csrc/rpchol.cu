@@ -156,21 +156,23 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D fp32 map over a row-major (rows x inner) array with leading dimension
-// `inner`, box box_inner x box_rows, the given swizzle, zero fill.
+// 2-D map over a row-major (rows x inner) FP32 (or FP16, `half`) array with
+// leading dimension `inner`, box box_inner x box_rows, the given swizzle,
+// zero fill.
 rpchol_status make_map(CUtensorMap* m, const void* base, unsigned long long inner,
                        unsigned long long rows, unsigned box_inner, unsigned box_rows,
-                       CUtensorMapSwizzle swz) {
+                       CUtensorMapSwizzle swz, bool half = false) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) {
     set_err("cuTensorMapEncodeTiled is unavailable");
     return RPCHOL_ECUDA;
   }
   cuuint64_t dims[2] = {inner, rows};
-  cuuint64_t strides[1] = {inner * 4ull};
+  cuuint64_t strides[1] = {inner * (half ? 2ull : 4ull)};
   cuuint32_t box[2] = {box_inner, box_rows};
   cuuint32_t es[2] = {1u, 1u};
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = enc(m, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<void*>(base), dims, strides,
                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -552,7 +554,11 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
     // one 128 x kTMax-byte image per K chunk: ldF / 32 chunks of F(S,:), xld / 16 of X_S
     const size_t bfbytes = (size_t)(b.ldF / 32) * 128 * kTMax;
     const size_t bxbytes = (size_t)(b.xld / 16) * 128 * kTMax;
+    // FP16 heads / tails of 4096 F, the Schur contraction's A operand
+    const size_t fsbytes = 2 * sizeof(uint16_t) * (size_t)N * b.ldF;
     void* q;
+    if ((rs = dev_alloc(c, &q, fsbytes)) != RPCHOL_OK) return fail(rs);
+    m.Fsp = q;
     if ((rs = dev_alloc(c, &q, xbytes)) != RPCHOL_OK) return fail(rs);
     m.Xhp = (float*)q;
     if ((rs = dev_alloc(c, &q, xbytes)) != RPCHOL_OK) return fail(rs);
@@ -567,12 +573,15 @@ rpchol_status rpchol_create(int32_t kind, double sigma, const void* X, int64_t N
     m.Linv32 = (float*)q;
     m.err = (int*)((char*)b.st + offsetof(DevState, status));
     m.num_sms = b.num_sms;
-    e = cudaMemsetAsync(m.Bf, 0, bfbytes, c->stream);
+    // zero planes: the columns of a chunk beyond the rank meet zero B columns
+    e = cudaMemsetAsync(m.Fsp, 0, fsbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.Bf, 0, bfbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.Bx, 0, bxbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m.Linv32, 0, sizeof(float) * kTMax * kTMax, c->stream);
     if (e == cudaSuccess) e = launch_split_x(m, b, c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(e, "tensor-core operand setup"));
-    if ((rs = make_map(&m.F, b.F, b.ldF, N, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B)) != RPCHOL_OK)
+    if ((rs = make_map(&m.Fs, m.Fsp, 2ull * b.ldF, N, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B,
+                       true)) != RPCHOL_OK)
       return fail(rs);
     if ((rs = make_map(&m.Xh, m.Xhp, b.xld, N, 16, 128, CU_TENSOR_MAP_SWIZZLE_64B)) != RPCHOL_OK)
       return fail(rs);
@@ -853,6 +862,7 @@ rpchol_status rpchol_restore(rpchol_ctx* c, const void* host_buf, size_t bytes) 
     p += sizeof(long long) * rank;
     CU(cudaMemcpy2DAsync(c->b.F, es * c->b.ldF, p, es * rank, es * rank, c->b.N,
                          cudaMemcpyHostToDevice, c->stream));
+    if (c->use_tc) CU(launch_f16_planes(c->tc, c->b, rank, c->stream));
   }
   CU(cudaStreamSynchronize(c->stream));
   *c->st_host = st;
@@ -1030,6 +1040,7 @@ int64_t rpchol_context_bytes(int64_t N, int32_t d, int64_t k_max, int32_t T_max,
   b += 8LL * T_max * (ldF + kTMax);                   // extended operand rows
   if (mixed && N >= 128) {
     b += 2 * 4 * N * xld;                             // TF32 planes of X
+    b += 2 * 2 * N * ldF;                             // FP16 heads / tails of 4096 F
     b += (ldF / 32) * 128LL * kTMax + (xld / 16) * 128LL * kTMax;  // chunk images of F(S,:), X_S
     b += 4LL * kTMax + 4LL * kTMax * kTMax;
   }
