@@ -84,13 +84,7 @@ constexpr int kSmallBytes = 4 * 1024;     // pivots, their norms, barriers, flag
 constexpr int kTailBytes = 256;
 constexpr int kMaxStages = 6;
 constexpr int kMaxBuf = 4;                // tiles held in TMEM at once
-#ifndef RPCHOL_COLSTEP_PREFETCH
-#define RPCHOL_COLSTEP_PREFETCH 8
-#endif
-#ifndef RPCHOL_COLSTEP_W_RESIDENT
-#define RPCHOL_COLSTEP_W_RESIDENT 1
-#endif
-constexpr int kPrefetch = RPCHOL_COLSTEP_PREFETCH;  // chunks prefetched into L2 ahead of their loads
+
 constexpr float kFScale = 4096.f;         // the Schur operands are heads/tails of 4096 F
 constexpr float kAccScale = 16777216.f;   // 4096^2: the scale of the Schur products
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
@@ -117,7 +111,7 @@ __host__ __device__ inline Layout make_layout(int s) {
   int st_w = (budget - wbytes) / L.stage_bytes;
   if (st_w > kMaxStages) st_w = kMaxStages;
   const int want = st_nw < 3 ? st_nw : 3;
-  L.w_resident = (RPCHOL_COLSTEP_W_RESIDENT && st_w >= want) ? 1 : 0;
+  L.w_resident = st_w >= want ? 1 : 0;
   L.stages = L.w_resident ? st_w : st_nw;
   L.w_off = L.stages * L.stage_bytes;
   L.small_off = L.w_off + (L.w_resident ? wbytes : 0);
@@ -203,8 +197,10 @@ __device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float 
   for (int kp = 0; kp < 16; ++kp) {
     const int src = qbase | ((kp & 7) >> 1);
     const int cj = 2 * (kp >> 3) + (kp & 1);
-    const float2 w01 = *(const float2*)(Wblk + 16 * kp + 2 * cq);
-    const float2 w89 = *(const float2*)(Wblk + 16 * kp + 8 + 2 * cq);
+    // columns 2cq, 2cq + 1, 8 + 2cq, 9 + 2cq of row kp (stored together)
+    const float4 w = *(const float4*)(Wblk + 16 * kp + 4 * cq);
+    const float2 w01 = make_float2(w.x, w.y);
+    const float2 w89 = make_float2(w.z, w.w);
 #pragma unroll
     for (int ri = 0; ri < 4; ++ri) {
       const float xv = __shfl_sync(0xffffffffu, X[ri][cj], src);
@@ -517,24 +513,9 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
       tc::prefetch_tmap(tmFs);
       tc::prefetch_tmap(tmXh);
       tc::prefetch_tmap(tmXl);
-      // The A operands (rows of F and X, read once per round from HBM) are
-      // pulled into L2 kPrefetch chunks ahead of their shared-memory loads,
-      // so that a stage turns over at L2 rather than HBM latency.
-      Seq pf;
-      pf.init(ntl, nbuf, nXc, nF);
-      auto prefetch_next = [&]() {
-        while (!pf.done() && pf.kind() == 2) pf.next();
-        if (pf.done()) return;
-        const int prow = (int)((cta + (long long)pf.tile() * ncta) * kBM);
-        if (pf.kind() == 0) {
-          tc::tma_prefetch_2d(tmXh, pf.c * kXK, prow);
-          tc::tma_prefetch_2d(tmXl, pf.c * kXK, prow);
-        } else {
-          tc::tma_prefetch_2d(tmFs, pf.c * 2 * kFK, prow);
-        }
-        pf.next();
-      };
-      for (int i = 0; i < kPrefetch; ++i) prefetch_next();
+      // No L2 prefetch of the A operands ahead of their loads: measured, it
+      // slowed the stage turnover (the prefetches compete with the loads and
+      // the tensor cores' shared-memory reads for the same paths).
       long long g = 0;  // stages filled so far
       Seq sq;
       for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
@@ -563,7 +544,6 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
           tc::bulk_load_mc(sB + crank * sl, srcB + crank * sl, sl, &fullB[stg], mc_mask);
         }
         ++g;
-        if (kPrefetch > 0) prefetch_next();
       }
       if (mc > 1 && !*abort_flag) {
         // the last stages' releases by the other CTAs (multicast commits)
