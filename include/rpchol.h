@@ -369,7 +369,10 @@ rpchol_status rpchol_rpqr_destroy(rpchol_rpqr* ctx);
  *     launches).  Any precision.
  *
  * Both run each phase with the block decomposition rpchol_run uses, so an
- * instance's pivots and factor are bit-identical to rpchol_run's.  Each
+ * instance's pivots and factor are bit-identical to rpchol_run's.  The
+ * graph executor is the default (the faster of the two on the measured
+ * batches: the engine's control phases hold whole SMs while they wait on
+ * latency).  Each
  * context keeps its own buffers and results; after a batch run,
  * rpchol_stats / rpchol_factor / rpchol_copy_factor* on a context see that
  * context's run (its stream waits for the batch).
@@ -380,16 +383,16 @@ typedef struct rpchol_batch rpchol_batch;
 #define RPCHOL_BATCH_ENGINE 1
 
 /* Set up a batch of n >= 1 contexts (all on the current device) with block
- * sizes T[i] (1 <= T[i] <= that context's T_max): the engine when every
- * context supports it, else the graph.  The batch borrows the contexts:
+ * sizes T[i] (1 <= T[i] <= that context's T_max), recording the graph
+ * executor (the default mode).  The batch borrows the contexts:
  * destroy it before any of them.  Errors: EINVAL (n < 1, NULL context, T
  * out of range, a context twice), ENOMEM, ECUDA.                          */
 rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int32_t* T,
                                   rpchol_batch** out);
 
-/* Switch the executor for later runs (RPCHOL_BATCH_GRAPH records the graph
- * on first use).  Errors: EINVAL (unknown mode, or the engine when a member
- * does not support it), ENOMEM, ECUDA.                                     */
+/* Switch the executor for later runs (RPCHOL_BATCH_ENGINE sets up the
+ * engine's records on first use).  Errors: EINVAL (unknown mode, or the
+ * engine when a member does not support it), ENOMEM, ECUDA.                */
 rpchol_status rpchol_batch_set_mode(rpchol_batch* batch, int32_t mode);
 
 /* The executor in use; -1 for NULL.                                        */

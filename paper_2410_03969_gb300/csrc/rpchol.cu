@@ -1095,14 +1095,10 @@ rpchol_status rpchol_batch_create(rpchol_ctx* const* ctxs, int32_t n, const int3
     b->engine_ok = b->engine_ok && c->precision == RPCHOL_MIXED && c->use_tc &&
                    engine_supported(c->b, c->use_tc);
   }
-  rpchol_status rs;
-  if (b->engine_ok) {
-    rs = engine_prepare(b);
-    b->mode = RPCHOL_BATCH_ENGINE;
-  } else {
-    rs = batch_record(b);
-    b->mode = RPCHOL_BATCH_GRAPH;
-  }
+  // the graph executor is the default: on the measured batches it is the
+  // faster one (the engine is set up on first use, rpchol_batch_set_mode)
+  rpchol_status rs = batch_record(b);
+  b->mode = RPCHOL_BATCH_GRAPH;
   if (rs != RPCHOL_OK) return fail(rs);
   *out = b;
   return RPCHOL_OK;

@@ -45,9 +45,9 @@ def test_batch_equals_each_instance_alone(rp, precision, mode):
         f.run(p.k, T, s)
         alone.append(f.copy_factor())
     with rp.Batch(fs, Ts) as b:
-        # the engine is the default wherever every member supports it
-        assert b.mode == (rp.BATCH_ENGINE if precision == "mixed" else rp.BATCH_GRAPH)
+        assert b.mode == rp.BATCH_GRAPH  # the default executor
         b.mode = rp.BATCH_ENGINE if mode == "engine" else rp.BATCH_GRAPH
+        assert b.mode == (rp.BATCH_ENGINE if mode == "engine" else rp.BATCH_GRAPH)
         for rep in range(2):  # the same set-up serves repeated runs
             b.run([p.k for p in probs], seeds)
             for i, f in enumerate(fs):
@@ -80,7 +80,7 @@ def test_engine_queue_longer_than_grid(rp):
     fs = [rp.Factorizer(X, kern, 1.0, k_max=k, T_max=256, precision="mixed", instance=i)
           for i, (X, kern, k) in enumerate(probs)]
     with rp.Batch(fs, T) as b:
-        assert b.mode == rp.BATCH_ENGINE
+        b.mode = rp.BATCH_ENGINE
         for rep in range(2):
             ks = [max(1, k - 3 * rep) for (_, _, k) in probs]
             seeds = [77 + 5 * i + 1000 * rep for i in range(count)]
