@@ -87,7 +87,7 @@ _COLSTEP_TRAFFIC = {
     ("mixture20_n1e5", "mixed"): (
         162153888.0, "04fcd24dcced58aeb93d85712943709620fd5bdf030f42de1d6c007425f931cb"),
     ("unif64_n1e6", "mixed"): (
-        8925080543.0, "8222347ebc35195dcde9f078fff6a2dd79bfe920f1d340dbb1a5ed331d79fbb6"),
+        9925631431.0, "fb049b6d2a9723be7580f6a5e60bea6b210b178c5fe24ac83ff37e4533dea2c6"),
 }
 
 
