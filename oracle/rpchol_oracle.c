@@ -71,6 +71,23 @@
 #include <omp.h>
 #endif
 
+/* Residual floor (the paper stops when the weights sum to 0, in exact
+ * arithmetic): a residual weight at or below ORC_D_FLOOR (relative to the
+ * largest diagonal entry, 1 for the kernels) is rounding noise on an
+ * exhausted row; it is set to 0 together with the clamp at 0.  Without it
+ * a numerically rank-deficient kernel matrix keeps a few weights near
+ * 1e-16 whose recomputed Schur diagonals are far smaller, so Algorithm 1
+ * rejects them round after round and the run never stops.                  */
+#define ORC_D_FLOOR 1e-12
+
+/* The floor for weights that start at d (times the largest of them).      */
+static double orc_floor(const double* d, int64_t N)
+{
+    double m = 0.0;
+    for (int64_t j = 0; j < N; ++j) m = d[j] > m ? d[j] : m;
+    return ORC_D_FLOOR * m;
+}
+
 #define ORC_OK 0
 #define ORC_EINVAL 1
 #define ORC_ENOMEM 2
@@ -293,6 +310,7 @@ static int rpc_plain_impl(const orc_matrix* M, int64_t k, uint64_t seed, uint32_
     if (k < 0 || k > N) return ORC_EINVAL;
     memset(F, 0, sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
     for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    const double dfloor = orc_floor(d, N);
     double* g = (double*)malloc(sizeof(double) * (size_t)N);
     if (!g) return ORC_ENOMEM;
     int64_t rank = 0;
@@ -322,7 +340,7 @@ static int rpc_plain_impl(const orc_matrix* M, int64_t k, uint64_t seed, uint32_
             double f = g[r] / piv;
             F[r * k + i] = f;
             double v = d[r] - f * f;
-            d[r] = v > 0.0 ? v : 0.0;
+            d[r] = v > dfloor ? v : 0.0;
         }
         rank = i + 1;
     }
@@ -351,6 +369,7 @@ static int rpc_accel_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t max
         d[j] = orc_entry(M, j, j);
         if (dpre) dpre[j] = d[j];
     }
+    const double dfloor = orc_floor(d, N);
     int64_t* prop = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
     double* u = (double*)malloc(sizeof(double) * (size_t)T);
     double* ua = (double*)malloc(sizeof(double) * (size_t)T);
@@ -422,7 +441,7 @@ static int rpc_accel_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t max
             }
             double v = d[r] - rsq;
             if (dpre) dpre[r] = v;
-            d[r] = v > 0.0 ? v : 0.0;
+            d[r] = v > dfloor ? v : 0.0;
             free(Gheap);
         }
         rank += n;
@@ -453,6 +472,7 @@ static int rpc_block_impl(const orc_matrix* M, int64_t k, int32_t b, int64_t max
     if (k < 0 || k > N || b < 1) return ORC_EINVAL;
     memset(F, 0, sizeof(double) * (size_t)N * (size_t)(k > 0 ? k : 1));
     for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    const double dfloor = orc_floor(d, N);
     int64_t* Su = (int64_t*)malloc(sizeof(int64_t) * (size_t)b);   /* S' after Unique */
     double* Gs = (double*)malloc(sizeof(double) * (size_t)b * b);  /* G(S',:), then R^* */
     int32_t* keep = (int32_t*)malloc(sizeof(int32_t) * (size_t)b);
@@ -486,7 +506,7 @@ static int rpc_block_impl(const orc_matrix* M, int64_t k, int32_t b, int64_t max
         int32_t n = 0;
         for (int32_t i = 0; i < m; ++i) {
             double gii = Gs[(int64_t)i * m + i];
-            if (n >= k - rank || !(gii > 0.0)) continue;
+            if (n >= k - rank || !(gii > dfloor)) continue;  /* no pivot on rounding noise */
             keep[n++] = i;
             double piv = sqrt(gii);
             for (int32_t j = i; j < m; ++j) Gs[(int64_t)j * m + i] /= piv;
@@ -520,7 +540,7 @@ static int rpc_block_impl(const orc_matrix* M, int64_t k, int32_t b, int64_t max
                 rsq += G[a] * G[a];
             }
             double v = d[r] - rsq;
-            d[r] = v > 0.0 ? v : 0.0;
+            d[r] = v > dfloor ? v : 0.0;
             free(Gheap);
         }
         rank += n;
@@ -553,6 +573,7 @@ static int rpc_lowmem_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t ma
     const int64_t kk = k > 0 ? k : 1;
     memset(Lout, 0, sizeof(double) * (size_t)kk * (size_t)kk);
     for (int64_t j = 0; j < N; ++j) d[j] = orc_entry(M, j, j);
+    const double dfloor = orc_floor(d, N);
     int64_t* prop = (int64_t*)malloc(sizeof(int64_t) * (size_t)T);
     double* u = (double*)malloc(sizeof(double) * (size_t)T);
     double* ua = (double*)malloc(sizeof(double) * (size_t)T);
@@ -630,7 +651,7 @@ static int rpc_lowmem_impl(const orc_matrix* M, int64_t k, int32_t T, int64_t ma
                 rsq += g[a] * g[a];
             }
             double v = d[r] - rsq;
-            d[r] = v > 0.0 ? v : 0.0;
+            d[r] = v > dfloor ? v : 0.0;
             free(gheap);
         }
         /* L <- [L 0; Y(:,acc)^* L_i] */

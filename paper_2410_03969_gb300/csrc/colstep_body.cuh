@@ -730,7 +730,7 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
       double dn = 0.0;
       if (live) {
         const double v = dold - mysq;
-        dn = (v > 0.0 && myjp < 0) ? v : 0.0;
+        dn = (v > kDFloorMixed && myjp < 0) ? v : 0.0;
         a.dvec[grow] = dn;
       }
       for (int o = 16; o > 0; o >>= 1) dn += __shfl_down_sync(0xffffffffu, dn, o);

@@ -14,6 +14,19 @@ namespace rpchol {
 constexpr int kTileRows = 128;
 // Largest block size T (Algorithm 2's b).
 constexpr int kTMax = 256;
+// Residual weights at or below the floor (relative to the kernels' unit
+// diagonal) are rounding noise on an exhausted row and are set to 0 with the
+// clamp d <- max(d, 0).  Without it a numerically rank-deficient kernel
+// matrix keeps a few weights at the noise level whose recomputed Schur
+// diagonals are far smaller, so Algorithm 1 rejects them round after round
+// and the run never reaches its rank.  FP64 mode uses the oracle's floor; the
+// FP32 factor of mixed mode leaves noise near 1e-7 in d.
+constexpr double kDFloor64 = 1e-12;
+constexpr double kDFloorMixed = 4e-6;
+template <typename TF>
+__host__ __device__ __forceinline__ constexpr double d_floor() {
+  return sizeof(TF) == 8 ? kDFloor64 : kDFloorMixed;
+}
 // most ways the rank dimension of H = A(S',S') - F(S',:)F(S',:)^* is split
 constexpr int kHSplitMax = 8;
 constexpr int kHTilesMax = (kTMax / 16) * (kTMax / 16 + 1) / 2;

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_colstep_simt(
     const long long gr = row0 + tid;
     if (gr < N) {
       const double v = dvec[gr] - rsq;
-      dn = v > 0.0 ? v : 0.0;
+      dn = v > d_floor<TR>() ? v : 0.0;
       dvec[gr] = dn;
     }
   }

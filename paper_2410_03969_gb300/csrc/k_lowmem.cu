@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256)
       double t = 0.0;
       for (int q = 0; q < 16; ++q) t += rowsq[tid][q];
       const double v = dvec[gr] - t;
-      dn = v > 0.0 ? v : 0.0;
+      dn = v > kDFloor64 ? v : 0.0;
       dvec[gr] = dn;
     }
   }

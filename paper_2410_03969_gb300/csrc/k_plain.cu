@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kTileRows) k_plain_finish(
       F[r * ldF + i] = f;
       const double ff = (double)f;
       const double v = dv - ff * ff;
-      dv = v > 0.0 ? v : 0.0;
+      dv = v > d_floor<TF>() ? v : 0.0;
     } else {
       F[r * ldF + i] = (TF)0;
       if (r == s) dv = 0.0;

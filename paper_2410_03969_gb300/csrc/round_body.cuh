@@ -700,11 +700,12 @@ __device__ __forceinline__ void reject_body(RejSmem& R, double* Hown, DevState* 
       if (block) {
         // Algorithm 7: Unique keeps the first draw of each index (threshold
         // +inf: never accepted) and the Cholesky of H takes every other draw
-        // whose Schur residual is positive (threshold +0)
+        // whose Schur residual is above the residual floor (a residual at
+        // the rounding level is not a pivot)
         const int pi = prop[i];
         bool dup = false;
         for (int j = 0; j < i; ++j) dup |= prop[j] == pi;
-        u = dup ? 0x7ff0000000000000ll : 0;
+        u = dup ? 0x7ff0000000000000ll : __double_as_longlong(fp64 ? kDFloor64 : kDFloorMixed);
       } else {
         u = __double_as_longlong(uprop[i] * uacc[i]);
       }

@@ -590,3 +590,34 @@ def test_points_and_matrix_paths_agree():
     b = oracle.rpc_accel(20, 5, 8, A=A)
     assert list(a["S"]) == list(b["S"])
     assert np.array_equal(a["F"], b["F"])
+
+
+@pytest.mark.parametrize("algo", ["accel", "block", "plain", "lowmem"])
+def test_rank_deficient_kernel_stops_at_its_numerical_rank(algo):
+    """The residual floor: 1-D points under a Gaussian kernel give a kernel matrix
+    of numerical rank about 20.  Every run must stop there with all weights
+    at zero, long before the round limit, with the residual below the floor
+    and every accepted pivot's column well scaled (no pivot taken on
+    rounding noise)."""
+    X = np.random.default_rng(11).standard_normal((300, 1)).astype(np.float32)
+    A = oracle.kernel_matrix(X, "gaussian", 1.0)
+    ev = np.linalg.eigvalsh(A)
+    numrank = int(np.sum(ev > 1e-13 * ev[-1]))
+    k = 130
+    if algo == "accel":
+        o = oracle.rpc_accel(k, 16, 77, X=X, kernel="gaussian", sigma=1.0, max_rounds=4 * k + 64)
+    elif algo == "block":
+        o = oracle.rpc_block(k, 16, 77, X=X, kernel="gaussian", sigma=1.0, max_rounds=4 * k + 64)
+    elif algo == "plain":
+        o = oracle.rpc_plain(k, 77, X=X, kernel="gaussian", sigma=1.0)
+    else:
+        o = oracle.rpc_lowmem(k, 16, 77, X=X, kernel="gaussian", sigma=1.0,
+                              max_rounds=4 * k + 64)
+    assert 5 <= o["rank"] <= numrank + 2
+    assert float(np.sum(o["d"])) == 0.0
+    if "rounds" in o and algo != "plain":
+        assert o["rounds"] < 4 * o["rank"] + 10
+    # the factor reproduces A to the level of the floor on every entry
+    if "F" in o:
+        F = o["F"]
+        assert np.max(np.abs(A - F @ F.T)) < 1e-6
