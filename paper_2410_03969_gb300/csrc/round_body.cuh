@@ -342,7 +342,7 @@ __host__ __device__ __forceinline__ int hmat32_blocks(int T) {
   return nb * (nb + 1) / 2;
 }
 __host__ __device__ __forceinline__ int hmat32_splits(int nblk) {
-  int ks = (32 + nblk - 1) / nblk;
+  int ks = (128 + nblk - 1) / nblk;  // about 128 CTAs: one wave over the SMs
   if (ks > kHSplitMax) ks = kHSplitMax;
   return ks < 1 ? 1 : ks;
 }
