@@ -10,7 +10,12 @@ times complete factorisations of the first instance of that class at every
 candidate T on the device (CUDA events, after one untimed run) and keeps
 the fastest.  Results are cached per class, in memory and optionally in a
 JSON file.  The tile shape of the column step is fixed (128-row tiles, one
-per TMEM lane), so T is the only tuned parameter.
+per TMEM lane), so T is the tuned parameter of a factorisation.
+
+For a batch, `choose_executor` times both executors (one CUDA graph with a
+conditional round loop per instance, or one persistent kernel over a device
+instance queue) on the batch itself and keeps the faster one: which wins
+depends on the mix of instance sizes.
 """
 from __future__ import annotations
 
@@ -18,7 +23,7 @@ import json
 import math
 import os
 
-from . import Factorizer
+from . import BATCH_ENGINE, BATCH_GRAPH, Factorizer
 
 CANDIDATES = (32, 64, 96, 120, 128, 160, 200, 256)
 
@@ -72,3 +77,31 @@ class Autotuner:
             with open(self.cache_path, "w") as f:
                 json.dump(self.cache, f, indent=1, sort_keys=True)
         return best
+
+
+def choose_executor(batch, k, seeds, repeats: int = 3):
+    """Time the batch on each executor it supports (after one untimed run
+    each), leave it on the faster one and return (mode, {mode: ms})."""
+    import torch
+    from . import RpcholError
+    stream = torch.cuda.current_stream()
+    times = {}
+    for mode in (BATCH_GRAPH, BATCH_ENGINE):
+        try:
+            batch.mode = mode
+        except RpcholError:
+            continue  # a member the engine cannot run
+        batch.run(k, seeds)
+        ms = []
+        for r in range(repeats):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            batch.run(k, [int(s) + 1 + r for s in seeds])
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        times[mode] = sorted(ms)[len(ms) // 2]
+    best = min(times, key=times.get)
+    batch.mode = best
+    return best, times

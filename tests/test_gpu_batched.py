@@ -163,3 +163,28 @@ def test_autotuner_picks_a_candidate_and_caches(rp, tmp_path):
     assert tuner.timings[key][T] == min(tuner.timings[key].values())
     again = autotune.Autotuner(candidates=(32, 64, 128), cache_path=str(tmp_path / "tune.json"))
     assert again.choose(p.X, p.kernel, p.sigma, p.k) == T
+
+
+def test_autotuner_picks_the_faster_executor(rp):
+    from paper_2410_03969_gb300 import autotune
+    probs, Ts = _instances(6)
+    fs = [rp.Factorizer(p.X, p.kernel, p.sigma, k_max=p.k, T_max=max(Ts), precision="mixed",
+                        instance=i) for i, p in enumerate(probs)]
+    ks = [p.k for p in probs]
+    seeds = [500 + i for i in range(len(fs))]
+    with rp.Batch(fs, Ts[:len(fs)]) as b:
+        mode, times = autotune.choose_executor(b, ks, seeds, repeats=1)
+        assert set(times) == {rp.BATCH_GRAPH, rp.BATCH_ENGINE}
+        assert mode == min(times, key=times.get) and b.mode == mode
+        b.run(ks, seeds)
+        assert all(f.stats()["status"] == 0 for f in fs)
+    for f in fs:
+        f.close()
+    # FP64 members: the engine is not offered, the graph is kept
+    fs = [rp.Factorizer(p.X, p.kernel, p.sigma, k_max=p.k, T_max=64, precision="fp64")
+          for p in probs[:2]]
+    with rp.Batch(fs, [32, 64]) as b:
+        mode, times = autotune.choose_executor(b, [p.k for p in probs[:2]], [1, 2], repeats=1)
+        assert mode == rp.BATCH_GRAPH and set(times) == {rp.BATCH_GRAPH}
+    for f in fs:
+        f.close()
