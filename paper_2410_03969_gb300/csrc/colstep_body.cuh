@@ -188,26 +188,61 @@ struct EpiQuad {
   float inv_sigma;
 };
 
-// acc[ri] (columns 2cq..2cq+1 and 8+2cq..9+2cq) += sum over the 16 columns
-// kappa of block X (held across the quad) of X[ri][kappa] W(kappa, col)
-__device__ __forceinline__ void quad_fma_block(float2 (&acc)[4][2], const float (&X)[4][4],
-                                               const float* Wblk, int lane, int cq) {
-  const int qbase = lane & ~3;
+// Partial products of one 16 x 16 block in the quad layout.  A thread holds
+// X for its 4 rows at its own 4 columns kappa of the block (2cq, 2cq + 1,
+// 8 + 2cq, 9 + 2cq), so with no exchange it can form, for every one of the
+// 16 output columns, the part of sum_kappa X[ri][kappa] W(kappa, col) that
+// runs over its own kappa: P[ri][q] holds output columns (2q, 2q + 1) in .x
+// and (8 + 2q, 9 + 2q) in .y, the columns quad lane q finally owns.  The
+// quad's four parts are added once a block of G is complete (quad_reduce).
+// Row kappa of a W block keeps owner q's four columns in 16-byte group
+// q ^ ((kappa >> 1) & 3), which is q ^ cq for this thread's rows, so the
+// four lanes of a quad read four different bank groups.
+__device__ __forceinline__ void quad_part_block(float4 (&P)[4][4], const float (&X)[4][4],
+                                                const float* Wblk, int cq) {
 #pragma unroll
-  for (int kp = 0; kp < 16; ++kp) {
-    const int src = qbase | ((kp & 7) >> 1);
-    const int cj = 2 * (kp >> 3) + (kp & 1);
-    // columns 2cq, 2cq + 1, 8 + 2cq, 9 + 2cq of row kp (stored together)
-    const float4 w = *(const float4*)(Wblk + 16 * kp + 4 * cq);
-    const float2 w01 = make_float2(w.x, w.y);
-    const float2 w89 = make_float2(w.z, w.w);
+  for (int cj = 0; cj < 4; ++cj) {
+    const float* wr = Wblk + 16 * (8 * (cj >> 1) + 2 * cq + (cj & 1));
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) {
-      const float xv = __shfl_sync(0xffffffffu, X[ri][cj], src);
-      const float2 x2 = make_float2(xv, xv);
-      acc[ri][0] = __ffma2_rn(x2, w01, acc[ri][0]);
-      acc[ri][1] = __ffma2_rn(x2, w89, acc[ri][1]);
+    for (int q = 0; q < 4; ++q) {
+      const float4 w = *(const float4*)(wr + 4 * (q ^ cq));
+      const float2 w01 = make_float2(w.x, w.y), w89 = make_float2(w.z, w.w);
+#pragma unroll
+      for (int ri = 0; ri < 4; ++ri) {
+        const float2 x2 = make_float2(X[ri][cj], X[ri][cj]);
+        float2 lo = make_float2(P[ri][q].x, P[ri][q].y);
+        float2 hi = make_float2(P[ri][q].z, P[ri][q].w);
+        lo = __ffma2_rn(x2, w01, lo);
+        hi = __ffma2_rn(x2, w89, hi);
+        P[ri][q] = make_float4(lo.x, lo.y, hi.x, hi.y);
+      }
     }
+  }
+}
+
+// Sum the quad's four parts of every output column onto the lane that owns
+// it (two exchange steps: lanes cq ^ 2, then cq ^ 1); G[ri][cj] gets
+// columns 2cq, 2cq + 1, 8 + 2cq, 9 + 2cq, the quad layout's order.
+__device__ __forceinline__ void quad_reduce(const float4 (&P)[4][4], int cq, float (&G)[4][4]) {
+  const bool hi = (cq & 2) != 0, lo = (cq & 1) != 0;
+#pragma unroll
+  for (int ri = 0; ri < 4; ++ri) {
+    float4 k[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float4 snd = hi ? P[ri][q] : P[ri][q + 2];
+      const float4 kp = hi ? P[ri][q + 2] : P[ri][q];
+      k[q].x = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 2);
+      k[q].y = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 2);
+      k[q].z = kp.z + __shfl_xor_sync(0xffffffffu, snd.z, 2);
+      k[q].w = kp.w + __shfl_xor_sync(0xffffffffu, snd.w, 2);
+    }
+    const float4 snd = lo ? k[0] : k[1];
+    const float4 kp = lo ? k[1] : k[0];
+    G[ri][0] = kp.x + __shfl_xor_sync(0xffffffffu, snd.x, 1);
+    G[ri][1] = kp.y + __shfl_xor_sync(0xffffffffu, snd.y, 1);
+    G[ri][2] = kp.z + __shfl_xor_sync(0xffffffffu, snd.z, 1);
+    G[ri][3] = kp.w + __shfl_xor_sync(0xffffffffu, snd.w, 1);
   }
 }
 
@@ -280,13 +315,15 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
   for (int bi = 0; bi < nblk; ++bi) {
     const int j0 = 16 * bi;
     const float* Wb = e.W + 128 * bi * (bi + 1);
-    float2 acc[4][2];
+    float4 P[4][4];
 #pragma unroll
-    for (int ri = 0; ri < 4; ++ri) acc[ri][0] = acc[ri][1] = make_float2(0.f, 0.f);
+    for (int ri = 0; ri < 4; ++ri)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) P[ri][q] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int lb = 0; lb < bi; ++lb) {
       float X[4][4];
       tc::tmem_ld_quad16(e.acc + 16 * lb, X);
-      quad_fma_block(acc, X, Wb + 256 * lb, e.lane, cq);
+      quad_part_block(P, X, Wb + 256 * lb, cq);
     }
     float R[4][4];
     tc::tmem_ld_quad16(e.acc + j0, R);
@@ -294,14 +331,11 @@ __device__ __forceinline__ void epi_tile_quad(const EpiQuad e, int nblk, float (
     for (int ri = 0; ri < 4; ++ri)
 #pragma unroll
       for (int cj = 0; cj < 4; ++cj) R[ri][cj] *= (1.f / kAccScale);
-    quad_fma_block(acc, R, Wb + 256 * bi, e.lane, cq);
+    quad_part_block(P, R, Wb + 256 * bi, cq);
     float G[4][4];
+    quad_reduce(P, cq, G);
 #pragma unroll
     for (int ri = 0; ri < 4; ++ri) {
-      G[ri][0] = acc[ri][0].x;
-      G[ri][1] = acc[ri][0].y;
-      G[ri][2] = acc[ri][1].x;
-      G[ri][3] = acc[ri][1].y;
       if (e.jpiv[ri] >= 0) {
         // A pivot row of this round: in exact arithmetic R(S,:) = L L^*, so
         // G(S_j,:) = L(j,:) and its residual is zero.  The exact values (L

@@ -143,10 +143,14 @@ __device__ __forceinline__ void prep_rows_strided(const DevState* st, const floa
 // One CTA per block b and part of the range l < j0 (part 0 also writes the
 // diagonal rows).  Each CTA forms D_b^{-1} itself, by rows (row c is final
 // once rows < c are), one step per row for the whole CTA.
-// Column jj of a 16-column W block is stored at position wpos(jj), so that
-// the four columns a thread of the column step's epilogue multiplies by
-// (2c, 2c + 1, 8 + 2c, 9 + 2c for quad lane c) are one 16-byte load.
-__device__ __forceinline__ int wpos(int jj) { return 4 * ((jj & 7) >> 1) + 2 * (jj >> 3) + (jj & 1); }
+// Column jj of row l of a 16-column W block is stored at position
+// wpos(l, jj): the four columns quad lane c of the column step's epilogue
+// owns (2c, 2c + 1, 8 + 2c, 9 + 2c) form one 16-byte group, and group c
+// sits at group slot c ^ ((l >> 1) & 3), so that the four lanes of a quad,
+// which read four rows l two apart, hit four different bank groups.
+__device__ __forceinline__ int wpos(int l, int jj) {
+  return 4 * (((jj & 7) >> 1) ^ ((l >> 1) & 3)) + 2 * (jj >> 3) + (jj & 1);
+}
 
 struct WblkSmem {
   double Db[16][17];
@@ -196,10 +200,10 @@ __device__ __forceinline__ void wblk(WblkSmem& S, const DevState* st,
     const int l = e >> 4, jj = e & 15;
     double a = 0.0;
     for (int mm = 0; mm <= jj; ++mm) a = fma(Dinv[jj][mm], Lb[mm][l], a);
-    Wb[(long long)(l0 + l) * 16 + wpos(jj)] = (float)(-a);
+    Wb[(long long)(l0 + l) * 16 + wpos(l0 + l, jj)] = (float)(-a);
   }
   if (part == 0)  // W_b(j0 + m, jj) = D_b^{-1}(jj, m)
-    Wb[(long long)(j0 + r) * 16 + wpos(m)] = (float)Dinv[m][r];
+    Wb[(long long)(j0 + r) * 16 + wpos(j0 + r, m)] = (float)Dinv[m][r];
 }
 
 // All of W block b in one pass of 256 threads: D_b^{-1} once, then the
@@ -241,11 +245,11 @@ __device__ __forceinline__ void wblk_full(WblkSmem& S, const DevState* st, const
       const int l = e >> 4, jj = e & 15;
       double a = 0.0;
       for (int mm = 0; mm <= jj; ++mm) a = fma(Dinv[jj][mm], Lb[mm][l], a);
-      Wb[(long long)(l0 + l) * 16 + wpos(jj)] = (float)(-a);
+      Wb[(long long)(l0 + l) * 16 + wpos(l0 + l, jj)] = (float)(-a);
     }
     body_sync();
   }
-  Wb[(long long)(j0 + r) * 16 + wpos(m)] = (float)Dinv[m][r];
+  Wb[(long long)(j0 + r) * 16 + wpos(j0 + r, m)] = (float)Dinv[m][r];
 }
 
 // One launch for both: CTAs [0, kTMax) prepare the rows of the B operands,
