@@ -126,8 +126,11 @@ __host__ __device__ inline Layout make_layout(int s) {
 // or more tiles in TMEM split = 0 (the next tile's distances and kappa pass
 // run while this tile's Schur MMAs execute); with two, the next tile's
 // buffer frees only when the epilogue of tile t - 1 is done, so its X chunks
-// come two thirds of the way through tile t's F chunks.  Producer and MMA
-// issuer walk the same sequence.
+// come nine tenths of the way through tile t's F chunks (measured against
+// 1/2, 2/3, 3/4 and 5/6: the later the split, the longer the final pass of
+// tile t - 1 may take without stalling the tensor cores, while the last
+// tenth still covers the next tile's kappa pass).  Producer and MMA issuer
+// walk the same sequence.
 struct Seq {
   int t, ph, c;  // ph 0: F(t) before the split, 1: X(t + 1), 2: F(t) after it
   int ntl, nXc, nF, nFi, split;
@@ -136,7 +139,7 @@ struct Seq {
     nXc = nXc_;
     nF = nF_;
     nFi = nF > 0 ? nF : 1;
-    split = nbuf >= 3 ? 0 : (2 * nFi) / 3;
+    split = nbuf >= 3 ? 0 : (9 * nFi) / 10;
     t = -1;
     ph = 0;
     c = 0;
