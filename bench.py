@@ -637,9 +637,10 @@ def small_measure(rp, stream, seeds=100):
 
 def e2e_measure(rp, prob, prec, steps, seed_base):
     """End to end through the public API: create a context from pinned host X
-    (copied to the device by rpchol_create), run to rank k, copy F and the
-    pivots to pinned host memory (rpchol_copy_factor_raw), destroy; host wall
-    clock per step, every copy inside."""
+    (copied to the device by rpchol_create), run to rank k with F streamed to
+    pinned host memory round by round (rpchol_run_to_host: the copy engine
+    moves each round's columns while later rounds compute), destroy; host
+    wall clock per step, every copy inside."""
     import torch
     Xh = torch.from_numpy(prob.X).pin_memory()
     es = 4 if prec == "mixed" else 8
@@ -652,15 +653,14 @@ def e2e_measure(rp, prob, prec, steps, seed_base):
         t0 = time.perf_counter()
         with rp.Factorizer(Xh, prob.kernel, prob.sigma, k_max=prob.k, T_max=prob.T,
                            precision=prec) as g:
-            g.run(prob.k, prob.T, seed_base + i)
-            g.copy_factor_raw(Fh.data_ptr(), prob.k, Ph.data_ptr())
+            g.run_to_host(prob.k, prob.T, seed_base + i, Fh.data_ptr(), prob.k, Ph.data_ptr())
         em.append(time.perf_counter() - t0)
     e2e_t = statistics.median(em)
     return {"value": prob.k / e2e_t, "unit": UNIT, "ms_p50": e2e_t * 1e3, "steps": steps,
             "h2d_bytes_per_step": int(prob.X.nbytes),
             "d2h_bytes_per_step": int(prob.N * prob.k * es + prob.k * 8),
-            "path": "rpchol_create from pinned host X, rpchol_run, rpchol_copy_factor_raw to "
-                    "pinned host F and pivots, destroy"}
+            "path": "rpchol_create from pinned host X, rpchol_run_to_host to pinned host F and "
+                    "pivots (columns copied round by round during the run), destroy"}
 
 
 def ours_arm(args):

@@ -206,6 +206,23 @@ rpchol_status rpchol_copy_factor(rpchol_ctx* ctx, double* F_out, int64_t ld_out,
 rpchol_status rpchol_copy_factor_raw(rpchol_ctx* ctx, void* F_out, int64_t ld_out,
                                      int64_t* pivots_out);
 
+/* Accelerated RPCholesky (as rpchol_run) with the factor streamed to
+ * caller memory while the rounds run.  Columns of F never change once
+ * their round has ended (later rounds only append columns), so after each
+ * round the columns it added are copied, by the copy engine on a stream of
+ * the context's own, to F_out while the next rounds compute.  The rounds
+ * are launched from the host, a few ahead of the one whose end the host
+ * waits for (no CUDA graph).  On return F_out holds F as N x ld_out in the
+ * dtype F is stored in (FP32 in MIXED, FP64 in FP64 mode) and pivots_out
+ * the rank pivots; entries of F_out beyond the final rank are not written.
+ * Results are bit-identical to rpchol_run followed by
+ * rpchol_copy_factor_raw.  F_out and pivots_out: any memory the CUDA
+ * runtime can address (pinned host memory gives the copy engine's full
+ * rate); pivots_out may be NULL.  1 <= k <= k_max, 1 <= T <= T_max,
+ * ld_out >= k.  Synchronous; returns the run status as rpchol_sync does.  */
+rpchol_status rpchol_run_to_host(rpchol_ctx* ctx, int64_t k, int32_t T, uint64_t seed,
+                                 void* F_out, int64_t ld_out, int64_t* pivots_out);
+
 /* Statistics of the last run; computes the relative trace error
  * tr(A - F F^*)/tr(A) from F with FP64 accumulation.  Synchronous.        */
 rpchol_status rpchol_stats(rpchol_ctx* ctx, rpchol_run_stats* out);

@@ -77,6 +77,9 @@ _SIGNATURES = [
                                           ctypes.c_void_p, ctypes.c_void_p]),
     ("rpchol_copy_factor_raw", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.c_void_p]),
+    ("rpchol_run_to_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p]),
     ("rpchol_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RunStats)]),
     ("rpchol_destroy", None, [ctypes.c_void_p]),
     ("rpchol_save", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
@@ -326,6 +329,17 @@ class Factorizer:
         _check(lib().rpchol_copy_factor_raw(self._ctx, ctypes.c_void_p(F_out_ptr), int(ld_out),
                                             ctypes.c_void_p(piv_out_ptr) if piv_out_ptr
                                             else None), "rpchol_copy_factor_raw")
+
+    def run_to_host(self, k: int, T: int, seed: int, F_out_ptr: int, ld_out: int,
+                    piv_out_ptr: int | None = None):
+        """Accelerated RPCholesky with F streamed to caller memory (pinned host
+        memory for full speed) round by round while the later rounds compute;
+        synchronous, same results as run() followed by copy_factor_raw()."""
+        _check(lib().rpchol_run_to_host(self._ctx, int(k), int(T), int(seed) & (2**64 - 1),
+                                        ctypes.c_void_p(F_out_ptr), int(ld_out),
+                                        ctypes.c_void_p(piv_out_ptr) if piv_out_ptr else None),
+               "rpchol_run_to_host")
+        return self
 
     def stats(self) -> dict:
         st = RunStats()

@@ -91,6 +91,12 @@ struct rpchol_ctx {
   int gate_gen = 0;
   int use_tc = 0;             // mixed mode: tensor-core column step
   TcMaps tc{};
+  // rpchol_run_to_host: copy stream, pinned mapped ring of state snapshots
+  // (one per round in flight) and the events that mark each round done
+  cudaStream_t copy_stream = nullptr;
+  DevState* snap_host = nullptr;
+  cudaEvent_t snap_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t copy_ev = nullptr;
 };
 
 namespace {
@@ -134,6 +140,19 @@ void release_all(rpchol_ctx* c) {
   c->gate_host = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  c->copy_stream = nullptr;
+  for (cudaEvent_t& e : c->snap_ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  if (c->copy_ev) cudaEventDestroy(c->copy_ev);
+  c->copy_ev = nullptr;
+  if (c->snap_host) cudaFreeHost(c->snap_host);
+  c->snap_host = nullptr;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -389,6 +408,90 @@ rpchol_status status_of(const DevState& s) {
   return RPCHOL_OK;
 }
 
+// Rounds launched ahead of the one whose end the host waits for; the
+// snapshot ring holds one slot per round in flight.
+constexpr int kStreamAhead = 3;
+// Finished columns are copied once they make rows of at least this many
+// bytes: the copy engine moves N rows of 800 bytes (one round of 200 FP32
+// columns) at about 120 GB/s into pinned host memory and rows of 3200
+// bytes at about 190 GB/s, the link's rate.  Near the target rank every
+// round is copied at once, so that little is left after the last round.
+constexpr long long kFlushRowBytes = 3200;
+
+// Copy of the device state into mapped pinned host memory, written by a
+// kernel so that no copy engine (busy with the factor's columns) sits on
+// the round stream.
+__global__ void k_snapshot(const DevState* st, DevState* out) {
+  const int n = (int)(sizeof(DevState) / sizeof(int));
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    ((volatile int*)out)[i] = ((const volatile int*)st)[i];
+}
+
+// The round loop of rpchol_run_to_host (device state reset): after each
+// round the host reads that round's state snapshot and has the copy stream
+// move the columns the round added, while later rounds run.
+rpchol_status run_streaming(rpchol_ctx* c, long long k, int T, long long max_rounds,
+                            char* F_out, long long ld_out, int64_t* pivots_out) {
+  static_assert(kStreamAhead + 1 <= 4, "snapshot events");
+  static_assert(sizeof(DevState) % sizeof(int) == 0, "state copied as ints");
+  if (!c->copy_stream) {
+    CU(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    CU(cudaHostAlloc((void**)&c->snap_host, sizeof(DevState) * (kStreamAhead + 1),
+                     cudaHostAllocMapped));
+    for (cudaEvent_t& e : c->snap_ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming));
+  }
+  DevState* snap_dev = nullptr;
+  CU(cudaHostGetDevicePointer((void**)&snap_dev, c->snap_host, 0));
+  const size_t es = c->b.mixed ? sizeof(float) : sizeof(double);
+  long long launched = 0, waited = 0, copied = 0;
+  for (;;) {
+    while (launched < max_rounds + 1 && launched - waited <= kStreamAhead) {
+      const int slot = (int)(launched % (kStreamAhead + 1));
+      cudaError_t e = launch_body(c, 0, T, 0ull, 0, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "round launch");
+      k_snapshot<<<1, 64, 0, c->stream>>>(c->b.st, snap_dev + slot);
+      CU(cudaGetLastError());
+      CU(cudaEventRecord(c->snap_ev[slot], c->stream));
+      ++launched;
+      c->host_iters = launched;
+    }
+    if (waited == launched) break;
+    const int slot = (int)(waited % (kStreamAhead + 1));
+    CU(cudaEventSynchronize(c->snap_ev[slot]));
+    ++waited;
+    const volatile DevState& sn = c->snap_host[slot];
+    const long long rank = sn.rank;
+    const bool last = sn.done || sn.status || waited == launched;
+    const bool flush = last || (rank - copied) * (long long)es >= kFlushRowBytes ||
+                       (rank + kFlushRowBytes / (long long)es) >= k;
+    if (rank > copied && flush) {
+      // columns [copied, rank) are final: the copy engine moves them while
+      // the rounds already launched run
+      CU(cudaStreamWaitEvent(c->copy_stream, c->snap_ev[slot], 0));
+      CU(cudaMemcpy2DAsync(F_out + es * copied, es * ld_out, (const char*)c->b.F + es * copied,
+                           es * c->b.ldF, es * (rank - copied), c->b.N, cudaMemcpyDefault,
+                           c->copy_stream));
+      copied = rank;
+    }
+    if (sn.done || sn.status) break;  // rounds still in flight find the run done
+  }
+  CU(cudaEventRecord(c->copy_ev, c->stream));  // every launched round
+  CU(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0));
+  if (pivots_out && copied > 0)
+    CU(cudaMemcpyAsync(pivots_out, c->b.piv, sizeof(long long) * copied, cudaMemcpyDefault,
+                       c->copy_stream));
+  CU(cudaStreamSynchronize(c->copy_stream));
+  rpchol_status st = read_state(c);
+  if (st != RPCHOL_OK) return st;
+  if (c->st_host->rank != copied) {
+    set_err("rpchol_run_to_host: rank %lld at the end, %lld columns copied",
+            (long long)c->st_host->rank, copied);
+    return RPCHOL_ECUDA;
+  }
+  return status_of(*c->st_host);
+}
+
 }  // namespace
 
 extern "C" {
@@ -602,6 +705,22 @@ rpchol_status rpchol_run(rpchol_ctx* c, int64_t k, int32_t T, uint64_t seed) {
     return RPCHOL_EINVAL;
   }
   return run_common(c, 0, k, T, seed);
+}
+
+rpchol_status rpchol_run_to_host(rpchol_ctx* c, int64_t k, int32_t T, uint64_t seed,
+                                 void* F_out, int64_t ld_out, int64_t* pivots_out) {
+  g_err[0] = 0;
+  if (!c || k < 1 || k > c->k_max || T < 1 || T > c->b.Tmax || !F_out || ld_out < k) {
+    set_err("invalid argument: k=%lld T=%d F_out=%p ld_out=%lld", (long long)k, T, F_out,
+            (long long)ld_out);
+    return RPCHOL_EINVAL;
+  }
+  const long long max_rounds = 4 * k + 64;
+  clear_prof(c);
+  CU(launch_reset(c->b, k, T, seed, c->instance, 0, max_rounds, c->stream));
+  c->last_plain = 0;
+  c->has_run = 1;
+  return run_streaming(c, k, T, max_rounds, (char*)F_out, ld_out, pivots_out);
 }
 
 rpchol_status rpchol_run_block(rpchol_ctx* c, int64_t k, int32_t b, uint64_t seed) {
