@@ -203,12 +203,22 @@ struct EpiQuad {
 // four lanes of a quad read four different bank groups.
 __device__ __forceinline__ void quad_part_block(float4 (&P)[4][4], const float (&X)[4][4],
                                                 const float* Wblk, int cq) {
+  // the W row of the next own column is loaded before the products of the
+  // current one, so its shared-memory latency overlaps them
+  float4 wb[2][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) wb[0][q] = *(const float4*)(Wblk + 16 * (2 * cq) + 4 * (q ^ cq));
 #pragma unroll
   for (int cj = 0; cj < 4; ++cj) {
-    const float* wr = Wblk + 16 * (8 * (cj >> 1) + 2 * cq + (cj & 1));
+    if (cj < 3) {
+      const int cn = cj + 1;
+      const float* wn = Wblk + 16 * (8 * (cn >> 1) + 2 * cq + (cn & 1));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wb[cn & 1][q] = *(const float4*)(wn + 4 * (q ^ cq));
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 w = *(const float4*)(wr + 4 * (q ^ cq));
+      const float4 w = wb[cj & 1][q];
       const float2 w01 = make_float2(w.x, w.y), w89 = make_float2(w.z, w.w);
 #pragma unroll
       for (int ri = 0; ri < 4; ++ri) {
