@@ -87,7 +87,7 @@ _COLSTEP_TRAFFIC = {
     ("mixture20_n1e5", "mixed"): (
         162153888.0, "04fcd24dcced58aeb93d85712943709620fd5bdf030f42de1d6c007425f931cb"),
     ("unif64_n1e6", "mixed"): (
-        9936546743.0, "28a655c20e359f653b3ab9830e043364b3774fb7e24168b6d8bef507d4d9eea2"),
+        9929635109.0, "46d955d27a4363aae08c97133f8624b9f852d3df24cf3a44bb6d2b4054f2a815"),
 }
 
 
