@@ -210,7 +210,9 @@ rpchol_status rpchol_copy_factor_raw(rpchol_ctx* ctx, void* F_out, int64_t ld_ou
  * caller memory while the rounds run.  Columns of F never change once
  * their round has ended (later rounds only append columns), so after each
  * round the columns it added are copied, by the copy engine on a stream of
- * the context's own, to F_out while the next rounds compute.  The rounds
+ * the context's own, to F_out while the next rounds compute (whenever the
+ * copy stream is idle, else once the pending columns make rows of 3200
+ * bytes, so that each copy moves wide rows at the link's rate).  The rounds
  * are launched from the host, a few ahead of the one whose end the host
  * waits for (no CUDA graph).  On return F_out holds F as N x ld_out in the
  * dtype F is stored in (FP32 in MIXED, FP64 in FP64 mode) and pivots_out

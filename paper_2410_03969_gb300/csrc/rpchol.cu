@@ -14,6 +14,7 @@
 #include <map>
 #include <new>
 #include <vector>
+#include <atomic>
 
 #include "../../include/rpchol.h"
 #include "internal.h"
@@ -97,6 +98,7 @@ struct rpchol_ctx {
   DevState* snap_host = nullptr;
   cudaEvent_t snap_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t copy_ev = nullptr;
+  std::atomic<long long> copies_landed{0};  // 2-D copies the copy stream has finished
 };
 
 namespace {
@@ -411,12 +413,19 @@ rpchol_status status_of(const DevState& s) {
 // Rounds launched ahead of the one whose end the host waits for; the
 // snapshot ring holds one slot per round in flight.
 constexpr int kStreamAhead = 3;
-// Finished columns are copied once they make rows of at least this many
-// bytes: the copy engine moves N rows of 800 bytes (one round of 200 FP32
-// columns) at about 120 GB/s into pinned host memory and rows of 3200
-// bytes at about 190 GB/s, the link's rate.  Near the target rank every
-// round is copied at once, so that little is left after the last round.
+// Finished columns are copied as soon as the copy stream is idle, or once
+// they make rows of at least this many bytes: the copy engine moves N rows
+// of 800 bytes (one round of 200 FP32 columns) at about 120 GB/s into
+// pinned host memory and rows of 3200 bytes at about 190 GB/s, the link's
+// rate.  Copying whenever the engine is idle keeps it busy through the run
+// (the rows grow by themselves while a copy is in flight) and leaves about
+// one copy's worth of columns after the last round.
 constexpr long long kFlushRowBytes = 3200;
+
+// Host callback after each 2-D copy: counts the copies that have landed.
+void CUDART_CB copy_landed(void* p) {
+  ((std::atomic<long long>*)p)->fetch_add(1, std::memory_order_release);
+}
 
 // Copy of the device state into mapped pinned host memory, written by a
 // kernel so that no copy engine (busy with the factor's columns) sits on
@@ -430,8 +439,8 @@ __global__ void k_snapshot(const DevState* st, DevState* out) {
 // The round loop of rpchol_run_to_host (device state reset): after each
 // round the host reads that round's state snapshot and has the copy stream
 // move the columns the round added, while later rounds run.
-rpchol_status run_streaming(rpchol_ctx* c, long long k, int T, long long max_rounds,
-                            char* F_out, long long ld_out, int64_t* pivots_out) {
+rpchol_status run_streaming(rpchol_ctx* c, int T, long long max_rounds, char* F_out,
+                            long long ld_out, int64_t* pivots_out) {
   static_assert(kStreamAhead + 1 <= 4, "snapshot events");
   static_assert(sizeof(DevState) % sizeof(int) == 0, "state copied as ints");
   if (!c->copy_stream) {
@@ -445,6 +454,7 @@ rpchol_status run_streaming(rpchol_ctx* c, long long k, int T, long long max_rou
   CU(cudaHostGetDevicePointer((void**)&snap_dev, c->snap_host, 0));
   const size_t es = c->b.mixed ? sizeof(float) : sizeof(double);
   long long launched = 0, waited = 0, copied = 0;
+  long long issued = c->copies_landed.load(std::memory_order_acquire);
   for (;;) {
     while (launched < max_rounds + 1 && launched - waited <= kStreamAhead) {
       const int slot = (int)(launched % (kStreamAhead + 1));
@@ -463,8 +473,8 @@ rpchol_status run_streaming(rpchol_ctx* c, long long k, int T, long long max_rou
     const volatile DevState& sn = c->snap_host[slot];
     const long long rank = sn.rank;
     const bool last = sn.done || sn.status || waited == launched;
-    const bool flush = last || (rank - copied) * (long long)es >= kFlushRowBytes ||
-                       (rank + kFlushRowBytes / (long long)es) >= k;
+    const bool idle = c->copies_landed.load(std::memory_order_acquire) == issued;
+    const bool flush = last || idle || (rank - copied) * (long long)es >= kFlushRowBytes;
     if (rank > copied && flush) {
       // columns [copied, rank) are final: the copy engine moves them while
       // the rounds already launched run
@@ -472,6 +482,8 @@ rpchol_status run_streaming(rpchol_ctx* c, long long k, int T, long long max_rou
       CU(cudaMemcpy2DAsync(F_out + es * copied, es * ld_out, (const char*)c->b.F + es * copied,
                            es * c->b.ldF, es * (rank - copied), c->b.N, cudaMemcpyDefault,
                            c->copy_stream));
+      CU(cudaLaunchHostFunc(c->copy_stream, copy_landed, &c->copies_landed));
+      ++issued;
       copied = rank;
     }
     if (sn.done || sn.status) break;  // rounds still in flight find the run done
@@ -720,7 +732,7 @@ rpchol_status rpchol_run_to_host(rpchol_ctx* c, int64_t k, int32_t T, uint64_t s
   CU(launch_reset(c->b, k, T, seed, c->instance, 0, max_rounds, c->stream));
   c->last_plain = 0;
   c->has_run = 1;
-  return run_streaming(c, k, T, max_rounds, (char*)F_out, ld_out, pivots_out);
+  return run_streaming(c, T, max_rounds, (char*)F_out, ld_out, pivots_out);
 }
 
 rpchol_status rpchol_run_block(rpchol_ctx* c, int64_t k, int32_t b, uint64_t seed) {
