@@ -87,7 +87,7 @@ _COLSTEP_TRAFFIC = {
     ("mixture20_n1e5", "mixed"): (
         162153888.0, "04fcd24dcced58aeb93d85712943709620fd5bdf030f42de1d6c007425f931cb"),
     ("unif64_n1e6", "mixed"): (
-        9929635109.0, "46d955d27a4363aae08c97133f8624b9f852d3df24cf3a44bb6d2b4054f2a815"),
+        9929145539.0, "1106808795505e59c43592ca3c361331e1774b03e14c1f4b358c5d5115b5b437"),
 }
 
 
