@@ -563,14 +563,17 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
       // No L2 prefetch of the A operands ahead of their loads: measured, it
       // slowed the stage turnover (the prefetches compete with the loads and
       // the tensor cores' shared-memory reads for the same paths).
-      long long g = 0;  // stages filled so far
+      // stages filled so far, g = NS pass + stg, ph = pass & 1 (kept
+      // incrementally: a 64-bit division by the run-time NS on every stage
+      // costs this single lane hundreds of cycles)
+      long long g = 0;
+      int stg = 0;
+      uint32_t ph = 0;
       Seq sq;
       for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
         const int kd = sq.kind();
         if (kd == 2) continue;
-        const int stg = (int)(g % NS);
-        if (g >= NS && !tc::mbar_wait_bounded(&empty[stg], (uint32_t)(((g / NS) - 1) & 1),
-                                              kWaitNs, abort_flag))
+        if (g >= NS && !tc::mbar_wait_bounded(&empty[stg], ph ^ 1u, kWaitNs, abort_flag))
           break;
         const int row0 = (int)((cta + (long long)sq.tile() * ncta) * kBM);
         unsigned char* sA = sm + stg * SB;
@@ -591,6 +594,10 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
           tc::bulk_load_mc(sB + crank * sl, srcB + crank * sl, sl, &fullB[stg], mc_mask);
         }
         ++g;
+        if (++stg == NS) {
+          stg = 0;
+          ph ^= 1u;
+        }
       }
       if (mc > 1 && !*abort_flag) {
         // the last stages' releases by the other CTAs (multicast commits)
@@ -616,11 +623,20 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
     if (lane == 0) {
       const uint32_t id32 = tc::idesc_tf32(128, (uint32_t)s_pad);
       const uint32_t id16 = tc::idesc_f16(128, (uint32_t)s_pad);
-      long long g = 0;
+      // ring position kept incrementally, as in the producer; the tile's
+      // TMEM buffer and its use count change only with the tile
+      int stg = 0;
+      uint32_t ph = 0;
+      int jc = -1, b = 0;
+      uint32_t use = 0;
       Seq sq;
       for (sq.init(ntl, nbuf, nXc, nF); !sq.done() && !*abort_flag; sq.next()) {
-        const int kd = sq.kind(), j = sq.tile(), b = j % nbuf;
-        const uint32_t use = (uint32_t)(j / nbuf);
+        const int kd = sq.kind(), j = sq.tile();
+        if (j != jc) {
+          jc = j;
+          b = j % nbuf;
+          use = (uint32_t)(j / nbuf);
+        }
         const uint32_t acc = tbase + (uint32_t)(b * Lo.s_alloc);
         if (kd == 0 && sq.c == 0 && j >= nbuf) {  // the buffer's previous tile is done
           if (!tc::mbar_wait_bounded(&tfree[b], (use - 1) & 1, kWaitNs, abort_flag)) break;
@@ -634,8 +650,6 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
           tc::mma_commit(&accf[b]);
           continue;
         }
-        const int stg = (int)(g % NS);
-        const uint32_t ph = (uint32_t)((g / NS) & 1);
         if (!tc::mbar_wait_bounded(&full[stg], ph, kWaitNs, abort_flag) ||
             !tc::mbar_wait_bounded(&fullB[stg], ph, kWaitNs, abort_flag))
           break;
@@ -676,7 +690,10 @@ __device__ __forceinline__ bool colstep_body(const CUtensorMap* tmFs, const CUte
           else tc::mma_commit_mc(&empty[stg], mc_mask);
           if (sq.c == nF - 1) tc::mma_commit(&accf[b]);
         }
-        ++g;
+        if (++stg == NS) {
+          stg = 0;
+          ph ^= 1u;
+        }
       }
     }
   } else if (warp < 4) {
