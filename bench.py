@@ -87,7 +87,7 @@ _COLSTEP_TRAFFIC = {
     ("mixture20_n1e5", "mixed"): (
         162153888.0, "04fcd24dcced58aeb93d85712943709620fd5bdf030f42de1d6c007425f931cb"),
     ("unif64_n1e6", "mixed"): (
-        9929145539.0, "1106808795505e59c43592ca3c361331e1774b03e14c1f4b358c5d5115b5b437"),
+        9929326649.0, "5a3d05fb369c24f6a46e133306ec26fed88b42aeef509c009ebb5b267d901afb"),
 }
 
 
